@@ -1,0 +1,288 @@
+#!/usr/bin/env python
+"""Benchmark: gate bootstraps per second of CGGI gate bootstrapping on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl arx|reference]
+                    [--workload netlists|gates64|dag|matmul] [--mode graph|plain]
+
+A step is one evaluation of the workload's netlist through the C-ABI
+(arx_plan_run): every wave's blind rotations (mod switch, n CMux external
+products, sample extraction) and key switches, all on the GPU.  The default
+workload is the plain-netlist configuration: a 32-bit ripple-carry adder and an
+8x8-bit array multiplier (CGGI n=630, N=1024, Bg=2^7, l=3, key switch 2^2 x 8),
+evaluated one wave per launch.  Inputs are synthetic (seeded keys, bits, netlists).
+
+value   = bootstraps per step (MUX counts two) / mean device time per step,
+          inputs resident in HBM, L2 flushed (256 MiB write) between steps;
+e2e     = the same through the C-ABI with pinned HOST buffers (H2D of the inputs,
+          D2H of the outputs inside the timed region);
+latency = p50 / p99 of the per-step device time (netlist latency);
+roofline= the blind-rotation kernel's modular multiplications per second against
+          the IMAD-pipe peak (an integer-ALU roofline);
+cpu_baseline = the plain C oracle timed on this host's cores on a bounded sample.
+With --impl reference the oracle itself is the timed arm.
+Under torchrun (N > 1) every rank evaluates its own replica on its own GPU (no
+collective on the data path); value sums all ranks, time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2306_11006_gb300 import inputs as I  # noqa: E402
+
+METRIC = "gate bootstraps/sec on 1 GB300 (bit-exact vs oracle); netlist p50/p99 latency ms"
+LWE_N = 630
+# blind rotation work per bootstrap in 32-bit modular multiply-accumulates (two CRT
+# primes): per CMux, 8 length-1024 transforms x 5120 butterflies + 2 x 6 x 1024 MACs,
+# each once per prime.
+MODMUL_PER_CMUX = 2 * (8 * 5120 + 12 * 1024)
+# integer-ALU peak: 152 SMs x 2070 MHz x 64 IMAD lanes/clk / 3 IMADs per Shoup or
+# Montgomery modular multiply (derivation in the design doc)
+ALU_PEAK_TMODMUL = 152 * 2.070e9 * 64 / 3 / 1e12
+
+
+def workload(name: str):
+    if name == "netlists":
+        return I.union([I.ripple_carry_adder(32), I.array_multiplier(8)], name="adder32+mult8"), \
+            "32-bit ripple-carry adder + 8x8 array multiplier (plain netlists, one wave per launch)"
+    if name == "gates64":
+        t = I.random_gate_types(1, 64)
+        nl = I.Netlist(128, t, np.arange(64, dtype=np.uint32), np.arange(64, 128, dtype=np.uint32),
+                       np.zeros(64, np.uint32), np.arange(128, 192, dtype=np.uint32), "gates64")
+        return nl, "64 independent 2-input gates (one wave)"
+    if name == "dag":
+        return I.random_dag(seed=3), "random levelized DAG, 65,536 gates over 40 waves, 5% MUX"
+    if name == "matmul":
+        return I.union([I.matmul4x4() for _ in range(8)], name="8x matmul4x4"), \
+            "8 simultaneous 4x4 8-bit matrix products (16-bit accumulators), one launch per wave"
+    raise SystemExit(f"unknown workload {name}")
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    def __init__(self, gpu: int, path: str):
+        self.path, self.proc = path, None
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(nl, budget_s: float = 20.0):
+    """The plain C oracle on this host's cores, on a bounded sample of the workload's
+    bootstrapped gates (random inputs), in bootstraps per second."""
+    from oracle import oracle as O
+
+    n = LWE_N
+    kr = I.key_randomness(0, n)
+    bsk, ksk = O.keygen(kr)
+    ctx = O.Context(n, bsk, ksk)
+    cores = os.cpu_count() or 1
+    types = np.array([t for t in nl.type if I.BOOTSTRAPS[int(t)]], np.uint8)
+    if len(types) == 0:
+        types = np.array([I.NAND], np.uint8)
+    rng = np.random.default_rng(7)
+    done, boots, t0 = 0, 0, time.perf_counter()
+    batch = max(cores, 8)
+    while time.perf_counter() - t0 < budget_s / 2 or done == 0:
+        ts = types[rng.integers(0, len(types), batch)]
+        cts = []
+        for k in range(3):
+            m, e = I.encryption_randomness(100 + done + k, batch, n)
+            cts.append(O.encrypt(n, kr.s, m, e, I.random_bits(200 + done + k, batch)))
+        ctx.gates(ts, *cts, nthreads=cores)
+        done += batch
+        boots += int(sum(I.BOOTSTRAPS[int(t)] for t in ts))
+    dt = time.perf_counter() - t0
+    return {"value": boots / dt, "unit": "bootstraps/s", "cores": cores, "kind": "oracle",
+            "sample": f"{done} gates ({boots} bootstraps) drawn from the workload's gate types, "
+                      f"n={n}, {dt:.1f} s on {cores} threads"}
+
+
+def run_reference(args, nl, desc):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        cpu_baseline(nl, budget_s=2.0)
+    vals = [cpu_baseline(nl, budget_s=max(4.0, 60.0 / max(args.steps, 1))) for _ in range(args.steps)]
+    v = statistics.mean(x["value"] for x in vals)
+    boots = sum(I.BOOTSTRAPS[int(t)] for t in nl.type)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "bootstraps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * boots / v,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic", "config": {"workload": desc, "lwe_n": LWE_N},
+            "cpu_baseline": {"kind": "oracle", "cores": vals[0]["cores"], "sample": vals[0]["sample"], "value": v},
+            "e2e": {"value": v, "unit": "bootstraps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="arx", choices=["arx", "reference"])
+    ap.add_argument("--workload", default="netlists", choices=["netlists", "gates64", "dag", "matmul"])
+    ap.add_argument("--mode", default="graph", choices=["graph", "plain"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    nl, desc = workload(args.workload)
+    if args.impl == "reference":
+        return run_reference(args, nl, desc)
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2306_11006_gb300 import arx
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    # keys and inputs: client-side key generation and encryption from seeded randomness
+    n = LWE_N
+    kr = I.key_randomness(0, n)
+    bsk, ksk = arx.client_keygen(kr)
+    keyset = arx.load_keys(bsk, ksk, n)
+    bits = I.random_bits(1000 + rank, nl.num_inputs)
+    m, e = I.encryption_randomness(2000 + rank, nl.num_inputs, n)
+    ct_host = arx.client_encrypt(n, kr.s, m, e, bits)
+    ct_in = torch.from_numpy(ct_host.view(np.int32)).to(dev)
+    out = torch.zeros((len(nl.outputs), n + 1), dtype=torch.int32, device=dev)
+    mode = arx.MODE_GRAPH if args.mode == "graph" else arx.MODE_PLAIN
+    plan = arx.Plan(nl, keyset=keyset, mode=mode)
+    boots = plan.bootstraps
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    for _ in range(max(args.warmup, 1)):
+        plan.run(ct_in, out, stream)
+    torch.cuda.synchronize(dev)
+    truth = nl.plain_eval(bits)
+    verified = bool(np.array_equal(arx.client_decrypt(n, kr.s, out.cpu().numpy().view(np.uint32)), truth))
+
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    clocks = Clocks(local, os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")) \
+        if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else Clocks(local, f"/tmp/arx_clocks_{rank}.csv")
+    for k in range(args.steps):
+        flush.zero_()
+        evs[k][0].record(stream)
+        plan.run(ct_in, out, stream)
+        evs[k][1].record(stream)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ok = verified and np.array_equal(
+        arx.client_decrypt(n, kr.s, out.cpu().numpy().view(np.uint32)), truth)
+
+    # end to end through the C-ABI with pinned host buffers
+    host_in = torch.from_numpy(ct_host.view(np.int32).copy()).pin_memory()
+    host_out = torch.zeros((len(nl.outputs), n + 1), dtype=torch.int32).pin_memory()
+    e2e_s = []
+    for k in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        plan.run(host_in, host_out)
+        e2e_s.append(time.perf_counter() - t0)
+    e2e_ok = np.array_equal(arx.client_decrypt(n, kr.s, host_out.numpy().view(np.uint32)), truth)
+
+    # roofline of the dominant kernel (blind rotation), timed launch by launch
+    br_ms, ks_ms, br_l, ks_l = plan.profile(ct_in)
+    ops = boots * n * MODMUL_PER_CMUX
+    achieved = ops / (br_ms / 1e3) / 1e12
+    launches_per_step = br_l + ks_l + (1 if len(nl.outputs) else 0)
+
+    value = boots * args.steps * world / (total_ms / 1e3)
+    line = {
+        "metric": METRIC, "value": value, "unit": "bootstraps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": desc, "lwe_n": n, "N": 1024, "mode": args.mode, "gates": nl.num_gates,
+                   "bootstraps_per_step": boots, "waves": plan.waves,
+                   "l2": "flushed between steps (256 MiB write)", "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
+        "gates_per_s": nl.num_gates * args.steps * world / (total_ms / 1e3),
+        "verified": bool(ok and e2e_ok),
+        "e2e": {"value": boots / statistics.mean(e2e_s), "unit": "bootstraps/s",
+                "h2d_bytes_per_step": int(nl.num_inputs * (n + 1) * 4),
+                "d2h_bytes_per_step": int(len(nl.outputs) * (n + 1) * 4),
+                "p50_ms": 1e3 * float(np.percentile(e2e_s, 50))},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TMODMUL, "unit": "Tmodmul/s",
+                     "frac": achieved / ALU_PEAK_TMODMUL, "traffic": None, "kernel": "br_kernel",
+                     "kernel_ms_per_step": br_ms, "ks_ms_per_step": ks_ms},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk,
+    }
+    plan.close()
+    arx.unload_keys(keyset)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(nl)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

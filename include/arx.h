@@ -1,0 +1,200 @@
+/*
+ * arx.h -- C-ABI of libarx: CGGI gate bootstrapping over Boolean netlists on one
+ * NVIDIA GB300 (sm_103a).
+ *
+ * The method is that of "ArctyrEX: Accelerated Encrypted Execution of
+ * General-Purpose Applications" (arXiv 2306.11006): every encrypted logic gate is
+ * a linear pre-combination of LWE ciphertexts followed by a bootstrapping --
+ * blind rotation through n TGSW x TLWE external products -- and a key switch
+ * (Fig. 2, Sec. 2.2); a netlist is split into waves of independent gates that are
+ * evaluated one wave at a time (Sec. 4.2); keys are resident on the device and
+ * constant (Sec. 5.1).
+ *
+ * Parameters: N = 1024 (TLWE degree), k = 1, gadget Bg = 2^7 with l = 3, key
+ * switch base 2^2 with t = 8, Torus32 = uint32_t arithmetic mod 2^32.  The LWE
+ * dimension n is fixed per key set: 630 by default (Sec. 2.2), any 1..630
+ * through arx_load_keys_ex.  Encoding: bit 1 -> +1/8 (0x20000000), bit 0 -> -1/8.
+ *
+ * Layouts (all little-endian uint32_t, row-major, no padding):
+ *   LWE ciphertext   [n+1]: a_0 .. a_{n-1}, b  (phase = b - <a, s>)
+ *   bootstrapping key [n][6][2][N]: TGSW_K(s_i); row r = c*3 + (p-1) for
+ *                     c in {0: mask, 1: body}, gadget level p = 1..3; each row is
+ *                     a TLWE sample (mask polynomial, body polynomial).
+ *   key-switching key [N][8][4][n+1]: entry [i][j-1][v] = LWE_s(v K_i 2^(32-2j));
+ *                     the v = 0 entries are never read.
+ *
+ * Pointers: unless stated otherwise a ciphertext or key pointer may be host or
+ * device memory (classified with cudaPointerGetAttributes); it is borrowed for the
+ * duration of the call (or, for the _ex variants given a stream, until the work
+ * queued on that stream completes).  The library owns keys and workspace.
+ *
+ * Errors: every call returns ARX_OK (0) or a negative arx_status; nothing aborts
+ * the process; outputs are undefined after an error; arx_last_error() gives a
+ * thread-local message.  A device watchdog expiry (a bounded wait inside a kernel
+ * that ran out) is reported as ARX_ETIMEOUT by the synchronous calls and by
+ * arx_device_status().
+ *
+ * Threads and streams: calls are serialised by an internal lock.  Asynchronous
+ * (_ex with a non-NULL stream) calls on the same stream share that stream's
+ * workspace in stream order; calls on different streams use different
+ * workspaces.
+ */
+#ifndef ARX_H
+#define ARX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ARX_N 1024
+#define ARX_LWE_N 630
+#define ARX_BSK_ROWS 6
+#define ARX_KS_T 8
+#define ARX_KS_BASE 4
+#define ARX_MU 0x20000000u
+
+typedef enum {
+  ARX_OK = 0,
+  ARX_EINVAL = -1,    /* bad argument (size, type, wire id, pointer) */
+  ARX_ENOKEYS = -2,   /* no key set loaded / unknown key set id */
+  ARX_ENOMEM = -3,    /* device memory or HBM budget exhausted */
+  ARX_ECYCLE = -4,    /* netlist has a combinational cycle */
+  ARX_ETIMEOUT = -5,  /* a device-side bounded wait expired */
+  ARX_ECUDA = -6,     /* a CUDA runtime call failed */
+  ARX_EBUSY = -7      /* resource in use (key set referenced by a plan) */
+} arx_status;
+
+/* Gate opcodes: the standard two-input gates, the noiseless NOT, the MUX
+ * (Sec. 2.2) and the constant / copy gates of the runtime (Sec. 4.2). */
+typedef enum {
+  ARX_AND = 0, ARX_NAND, ARX_OR, ARX_NOR, ARX_XOR, ARX_XNOR,
+  ARX_NOT, ARX_MUX, ARX_COPY, ARX_CONST0, ARX_CONST1
+} arx_gate;
+
+/* ---------------------------------------------------------------- keys ---- */
+
+/* Copy a key pair to the device and carry the bootstrapping key into the NTT
+ * domain (done once; the paper keeps keys resident, Sec. 5.1).  Layouts above,
+ * n = 630.  Returns a key set id >= 0, or an error.  The most recently loaded key
+ * set is the default of the calls that take no key set id.  Synchronous. */
+int arx_load_keys(const uint32_t *bsk, const uint32_t *ksk);
+
+/* As arx_load_keys for LWE dimension lwe_n (1..630); stream may be NULL. */
+int arx_load_keys_ex(const uint32_t *bsk, const uint32_t *ksk, int lwe_n, void *stream);
+
+/* Free a key set.  ARX_EBUSY while a plan references it. */
+int arx_unload_keys(int keyset);
+
+/* Make a loaded key set the default of the calls that take no key set id. */
+int arx_use_keys(int keyset);
+
+/* Device bytes held by one key set of dimension lwe_n (NTT-domain BSK + KSK). */
+size_t arx_keyset_bytes(int lwe_n);
+
+/* ------------------------------------------------------------ gates ---- */
+
+/* count independent gates: ct_out[g] = types[g](ct_a[g], ct_b[g]) with the
+ * default key set.  types: host array of arx_gate (NOT / COPY read ct_a only,
+ * CONST read neither; MUX needs arx_bootstrap_gates_ex).  ct_*: [count][n+1].
+ * count = 0 is a no-op.  Synchronous. */
+int arx_bootstrap_gates(const uint8_t *types, const uint32_t *ct_a, const uint32_t *ct_b,
+                        uint32_t *ct_out, size_t count);
+
+/* As arx_bootstrap_gates with a MUX third input ct_c (MUX(a, b, c) = a ? b : c;
+ * may be NULL when no gate is a MUX), a key set id (-1 = default) and a CUDA
+ * stream (cudaStream_t; NULL = synchronous on the library's stream). */
+int arx_bootstrap_gates_ex(const uint8_t *types, const uint32_t *ct_a, const uint32_t *ct_b,
+                           const uint32_t *ct_c, uint32_t *ct_out, size_t count, int keyset,
+                           void *stream);
+
+/* ---------------------------------------------------------- netlists ---- */
+
+/* Gate netlist (host arrays).  Wire ids 0..num_inputs-1 are the inputs,
+ * num_inputs + g the output of gate g.  Gates may be listed in any order; in1 is
+ * read for two-input gates and MUX, in2 for MUX only (MUX(in0, in1, in2) =
+ * in0 ? in1 : in2).  outputs[o] is any wire id. */
+typedef struct {
+  uint32_t num_inputs, num_gates, num_outputs;
+  const uint8_t *type;
+  const uint32_t *in0, *in1, *in2;
+  const uint32_t *outputs;
+} arx_netlist;
+
+/* Wave levelization of Sec. 4.2 (host only, no GPU needed): wave[g] = 0 for a
+ * gate without gate inputs, else 1 + the largest wave of its gate inputs.
+ * *depth receives the number of waves.  ARX_EINVAL / ARX_ECYCLE on bad input. */
+int arx_levelize(const arx_netlist *nl, uint32_t *wave, uint32_t *depth);
+
+/* Evaluate a netlist with the default key set, wave by wave, one blind-rotation
+ * launch and one key-switch launch per wave.  ct_in [num_inputs][n+1],
+ * ct_out [num_outputs][n+1].  Synchronous. */
+int arx_eval_netlist(const arx_netlist *nl, const uint32_t *ct_in, uint32_t *ct_out);
+
+/* Execution modes of a plan. */
+#define ARX_MODE_PLAIN 0   /* per-wave launches, fixed heuristic shapes */
+#define ARX_MODE_GRAPH 1   /* autotuned persistent shapes, whole plan replayed as one CUDA graph */
+
+int arx_eval_netlist_ex(const arx_netlist *nl, const uint32_t *ct_in, uint32_t *ct_out, int keyset,
+                        int mode, void *stream);
+
+/* Plans: a netlist levelized and laid out on the device once, evaluated many
+ * times.  arx_plan_create copies the netlist (the caller's arrays may be freed
+ * afterwards) and returns a plan id >= 0.  Several netlists evaluated together
+ * are simply one netlist (their disjoint union): each wave then carries the
+ * ready gates of all of them in one launch. */
+int arx_plan_create(const arx_netlist *nl, int keyset, int mode);
+int arx_plan_run(int plan, const uint32_t *ct_in, uint32_t *ct_out, void *stream);
+int arx_plan_destroy(int plan);
+/* Describe a plan: waves, blind rotations, gates (any may be NULL). */
+int arx_plan_info(int plan, uint32_t *waves, uint64_t *bootstraps, uint64_t *gates);
+/* Copy wires of the plan's most recent evaluation: out[k] = wire ids[k]
+ * ([count][n+1]; ids host array, out host or device).  Synchronous.  Lets a
+ * caller inspect or checkpoint intermediate ciphertexts. */
+int arx_plan_wires(int plan, const uint32_t *ids, size_t count, uint32_t *out);
+
+/* Run the plan once, wave by wave without the graph, timing every launch with
+ * CUDA events on the library's stream: br_ms / ks_ms receive the summed
+ * durations of the blind-rotation and key-switch launches, br_launches /
+ * ks_launches their counts (any pointer may be NULL).  Outputs stay on the
+ * device.  Synchronous. */
+int arx_plan_profile(int plan, const uint32_t *ct_in, float *br_ms, float *ks_ms, uint32_t *br_launches,
+                     uint32_t *ks_launches);
+
+/* Force the blind-rotation launch shape: 2H warps per gate (H in 1, 2, 3, 6)
+ * and GT gates per CTA; (0, 0) restores the automatic choice.  Shapes:
+ * (6,1) (3,1) (3,2) (2,1) (2,3) (1,1) (1,2) (1,4) (1,6).  Plans keep the shapes
+ * chosen when they were created. */
+int arx_set_launch_shape(int H, int GT);
+
+/* ------------------------------------------------------------- status ---- */
+
+const char *arx_last_error(void);
+/* Reads and clears the device watchdog status: ARX_OK or ARX_ETIMEOUT. */
+int arx_device_status(void);
+/* Number of SMs of the device in use (0 before the first call that needs it). */
+int arx_device_sms(void);
+
+/* ------------------------------------------------------- client side ---- */
+/* Key generation, encryption and decryption as the client (the data owner)
+ * performs them (App. D: the server only ever sees ciphertexts and public
+ * keys).  All randomness is supplied by the caller; host memory only.
+ *   s [n] and K [N]: binary secret keys (bytes 0/1);
+ *   bsk_mask [n][6][N] uniform, bsk_noise [n][6][N] (Torus32 units);
+ *   ksk_mask [N][8][3][n] uniform, ksk_noise [N][8][3];
+ *   outputs in the layouts above. */
+int arx_client_keygen(int lwe_n, const uint8_t *s, const uint8_t *K, const uint32_t *bsk_mask,
+                      const int32_t *bsk_noise, const uint32_t *ksk_mask, const int32_t *ksk_noise,
+                      uint32_t *bsk, uint32_t *ksk);
+/* ct[g] = (mask[g], <mask[g], s> + noise[g] + (bits[g] ? +1/8 : -1/8)). */
+int arx_client_encrypt(int lwe_n, const uint8_t *s, const uint32_t *mask, const int32_t *noise,
+                       const uint8_t *bits, size_t count, uint32_t *ct);
+/* bits[g] = (int32)(b - <a, s>) > 0. */
+int arx_client_decrypt(int lwe_n, const uint8_t *s, const uint32_t *ct, size_t count, uint8_t *bits);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ARX_H */

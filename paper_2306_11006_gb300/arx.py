@@ -1,0 +1,264 @@
+"""Python binding of libarx (include/arx.h): argument marshalling only.
+
+Every step of gate bootstrapping runs in the CUDA kernels behind the C-ABI; this
+module turns numpy arrays and torch tensors (host or device) into pointers and
+return codes into exceptions.  PyTorch is only used for device memory and
+streams.  If libarx.so has not been built, every call raises: there is no
+fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libarx.so")
+
+N = 1024
+LWE_N = 630
+MU = 1 << 29
+AND, NAND, OR, NOR, XOR, XNOR, NOT, MUX, COPY, CONST0, CONST1 = range(11)
+MODE_PLAIN, MODE_GRAPH = 0, 1
+STATUS = {0: "ARX_OK", -1: "ARX_EINVAL", -2: "ARX_ENOKEYS", -3: "ARX_ENOMEM", -4: "ARX_ECYCLE",
+          -5: "ARX_ETIMEOUT", -6: "ARX_ECUDA", -7: "ARX_EBUSY"}
+
+# every entry point of include/arx.h with its ctypes signature
+_vp, _sz, _i, _u32, _u64 = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_uint32, ctypes.c_uint64
+
+
+class Netlist_C(ctypes.Structure):
+    _fields_ = [("num_inputs", _u32), ("num_gates", _u32), ("num_outputs", _u32), ("type", _vp),
+                ("in0", _vp), ("in1", _vp), ("in2", _vp), ("outputs", _vp)]
+
+
+_NLP = ctypes.POINTER(Netlist_C)
+SIGNATURES = {
+    "arx_load_keys": (_i, [_vp, _vp]),
+    "arx_load_keys_ex": (_i, [_vp, _vp, _i, _vp]),
+    "arx_unload_keys": (_i, [_i]),
+    "arx_use_keys": (_i, [_i]),
+    "arx_keyset_bytes": (_sz, [_i]),
+    "arx_bootstrap_gates": (_i, [_vp, _vp, _vp, _vp, _sz]),
+    "arx_bootstrap_gates_ex": (_i, [_vp, _vp, _vp, _vp, _vp, _sz, _i, _vp]),
+    "arx_levelize": (_i, [_NLP, _vp, _vp]),
+    "arx_eval_netlist": (_i, [_NLP, _vp, _vp]),
+    "arx_eval_netlist_ex": (_i, [_NLP, _vp, _vp, _i, _i, _vp]),
+    "arx_plan_create": (_i, [_NLP, _i, _i]),
+    "arx_plan_run": (_i, [_i, _vp, _vp, _vp]),
+    "arx_plan_destroy": (_i, [_i]),
+    "arx_plan_info": (_i, [_i, _vp, _vp, _vp]),
+    "arx_plan_wires": (_i, [_i, _vp, _sz, _vp]),
+    "arx_set_launch_shape": (_i, [_i, _i]),
+    "arx_plan_profile": (_i, [_i, _vp, _vp, _vp, _vp, _vp]),
+    "arx_last_error": (ctypes.c_char_p, []),
+    "arx_device_status": (_i, []),
+    "arx_device_sms": (_i, []),
+    "arx_client_keygen": (_i, [_i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "arx_client_encrypt": (_i, [_i, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "arx_client_decrypt": (_i, [_i, _vp, _vp, _sz, _vp]),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class ArxError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def lib():
+    """Load libarx.so (building it first when missing, where nvcc is available)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                from . import build as _build
+                _build.build()
+            h = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                f = getattr(h, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = h
+    return _lib
+
+
+def _check(rc: int) -> int:
+    if rc < 0:
+        raise ArxError(rc, lib().arx_last_error().decode(errors="replace"))
+    return rc
+
+
+def _ptr(x):
+    """Pointer of a numpy array or torch tensor (must be contiguous)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    raise TypeError(type(x))
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    return getattr(stream, "cuda_stream", stream)
+
+
+def _host_u8(x):
+    return np.ascontiguousarray(np.asarray(x, dtype=np.uint8))
+
+
+# ------------------------------------------------------------------- keys ---
+def load_keys(bsk, ksk, lwe_n: int = LWE_N, stream=None) -> int:
+    return _check(lib().arx_load_keys_ex(_ptr(bsk), _ptr(ksk), lwe_n, _stream(stream)))
+
+
+def unload_keys(keyset: int) -> None:
+    _check(lib().arx_unload_keys(keyset))
+
+
+def use_keys(keyset: int) -> None:
+    """Make a loaded key set the default of the calls that take no key set id."""
+    _check(lib().arx_use_keys(keyset))
+
+
+def keyset_bytes(lwe_n: int = LWE_N) -> int:
+    return int(lib().arx_keyset_bytes(lwe_n))
+
+
+# ------------------------------------------------------------------ gates ---
+def bootstrap_gates(types, ct_a, ct_b, ct_out) -> None:
+    t = _host_u8(types)
+    _check(lib().arx_bootstrap_gates(_ptr(t), _ptr(ct_a), _ptr(ct_b), _ptr(ct_out), len(t)))
+
+
+def bootstrap_gates_ex(types, ct_a, ct_b, ct_c, ct_out, keyset: int = -1, stream=None) -> None:
+    t = _host_u8(types)
+    _check(lib().arx_bootstrap_gates_ex(_ptr(t), _ptr(ct_a), _ptr(ct_b), _ptr(ct_c), _ptr(ct_out), len(t),
+                                        keyset, _stream(stream)))
+
+
+# --------------------------------------------------------------- netlists ---
+class _NetlistRef:
+    """Keeps the numpy arrays behind an arx_netlist alive."""
+
+    def __init__(self, nl):
+        u32 = lambda a: np.ascontiguousarray(np.asarray(a, dtype=np.uint32))
+        self.type = _host_u8(nl.type)
+        self.in0, self.in1, self.in2, self.outputs = u32(nl.in0), u32(nl.in1), u32(nl.in2), u32(nl.outputs)
+        self.c = Netlist_C(nl.num_inputs, len(self.type), len(self.outputs), _ptr(self.type), _ptr(self.in0),
+                           _ptr(self.in1), _ptr(self.in2), _ptr(self.outputs))
+
+    @property
+    def ref(self):
+        return ctypes.byref(self.c)
+
+
+def levelize(nl):
+    r = _NetlistRef(nl)
+    wave = np.zeros(max(len(r.type), 1), np.uint32)
+    depth = ctypes.c_uint32(0)
+    _check(lib().arx_levelize(r.ref, _ptr(wave), ctypes.addressof(depth)))
+    return wave[: len(r.type)], depth.value
+
+
+def eval_netlist(nl, ct_in, ct_out) -> None:
+    r = _NetlistRef(nl)
+    _check(lib().arx_eval_netlist(r.ref, _ptr(ct_in), _ptr(ct_out)))
+
+
+def eval_netlist_ex(nl, ct_in, ct_out, keyset: int = -1, mode: int = MODE_PLAIN, stream=None) -> None:
+    r = _NetlistRef(nl)
+    _check(lib().arx_eval_netlist_ex(r.ref, _ptr(ct_in), _ptr(ct_out), keyset, mode, _stream(stream)))
+
+
+class Plan:
+    """A netlist levelized and resident on the device, evaluated many times."""
+
+    def __init__(self, nl, keyset: int = -1, mode: int = MODE_GRAPH):
+        r = _NetlistRef(nl)
+        self.id = _check(lib().arx_plan_create(r.ref, keyset, mode))
+        w, b, g = ctypes.c_uint32(0), ctypes.c_uint64(0), ctypes.c_uint64(0)
+        _check(lib().arx_plan_info(self.id, ctypes.addressof(w), ctypes.addressof(b), ctypes.addressof(g)))
+        self.waves, self.bootstraps, self.gates = w.value, b.value, g.value
+
+    def run(self, ct_in, ct_out, stream=None) -> None:
+        _check(lib().arx_plan_run(self.id, _ptr(ct_in), _ptr(ct_out), _stream(stream)))
+
+    def wires(self, ids, n: int = LWE_N):
+        ids = np.ascontiguousarray(np.asarray(ids, dtype=np.uint32))
+        out = np.zeros((len(ids), n + 1), np.uint32)
+        _check(lib().arx_plan_wires(self.id, _ptr(ids), len(ids), _ptr(out)))
+        return out
+
+    def profile(self, ct_in):
+        """One wave-by-wave run timed per launch: (br_ms, ks_ms, br_launches, ks_launches)."""
+        bm, km = ctypes.c_float(0), ctypes.c_float(0)
+        bl, kl = ctypes.c_uint32(0), ctypes.c_uint32(0)
+        _check(lib().arx_plan_profile(self.id, _ptr(ct_in), ctypes.addressof(bm), ctypes.addressof(km),
+                                      ctypes.addressof(bl), ctypes.addressof(kl)))
+        return bm.value, km.value, bl.value, kl.value
+
+    def close(self) -> None:
+        if self.id is not None:
+            _check(lib().arx_plan_destroy(self.id))
+            self.id = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def set_launch_shape(H: int = 0, GT: int = 0) -> None:
+    """Force the blind-rotation launch shape; (0, 0) = automatic."""
+    _check(lib().arx_set_launch_shape(H, GT))
+
+
+def device_status() -> int:
+    return lib().arx_device_status()
+
+
+def device_sms() -> int:
+    return lib().arx_device_sms()
+
+
+# ------------------------------------------------------------ client side ---
+def client_keygen(kr):
+    """Key pair from an inputs.KeyRandomness: (bsk [n][6][2][N], ksk [N][8][4][n+1])."""
+    n = kr.n
+    bsk = np.zeros((n, 6, 2, N), np.uint32)
+    ksk = np.zeros((N, 8, 4, n + 1), np.uint32)
+    arrs = [np.ascontiguousarray(a) for a in (kr.s, kr.K, kr.bsk_mask, kr.bsk_noise, kr.ksk_mask, kr.ksk_noise)]
+    _check(lib().arx_client_keygen(n, *[_ptr(a) for a in arrs], _ptr(bsk), _ptr(ksk)))
+    return bsk, ksk
+
+
+def client_encrypt(n: int, s, mask, noise, bits):
+    bits = _host_u8(bits)
+    s = _host_u8(s)
+    mask = np.ascontiguousarray(mask, dtype=np.uint32)
+    noise = np.ascontiguousarray(noise, dtype=np.int32)
+    ct = np.zeros((len(bits), n + 1), np.uint32)
+    _check(lib().arx_client_encrypt(n, _ptr(s), _ptr(mask), _ptr(noise), _ptr(bits), len(bits), _ptr(ct)))
+    return ct
+
+
+def client_decrypt(n: int, s, ct):
+    ct = np.ascontiguousarray(np.asarray(ct, dtype=np.uint32)).reshape(-1, n + 1)
+    s = _host_u8(s)
+    bits = np.zeros(len(ct), np.uint8)
+    _check(lib().arx_client_decrypt(n, _ptr(s), _ptr(ct), len(ct), _ptr(bits)))
+    return bits

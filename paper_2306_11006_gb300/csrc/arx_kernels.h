@@ -1,0 +1,104 @@
+// arx_kernels.h -- internal interface between the host engine and the kernels.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+namespace arx {
+
+constexpr int kN = 1024;          // TLWE ring degree
+constexpr int kMaxLweN = 630;     // largest LWE dimension the device layouts hold
+constexpr int kWireStride = 632;  // words per LWE_n ciphertext in device buffers
+constexpr int kOutStride = 1028;  // words per extracted LWE_N sample
+constexpr int kKsRowStride = 632; // words per key-switching-key row
+constexpr int kChunkWords = 2 * 2 * kN;       // one BSK row: [c_out 2][prime 2][N]
+constexpr int kChunkBytes = kChunkWords * 4;  // 16 KiB
+constexpr uint32_t kQ0 = 195198977u;
+constexpr uint32_t kQ1 = 195188737u;
+
+
+// Twiddles.  Forward zeta[k] = psi^bitrev10(k) (k = 1..1023), psi a primitive
+// 2048-th root of unity mod q; the stage with m blocks uses zeta[m + block].
+// The warp-uniform ones travel in the kernel parameter block (constant bank),
+// the per-lane ones in global memory.
+struct TwiddleConst {
+  uint2 fwd1[2][32];  // pass-1 forward zetas, index 1..31, (w, floor(w 2^32 / q))
+  uint2 inv2[2][32];  // pass-2 inverse zetas, index 1..31
+};
+
+struct TwiddleGlobal {
+  uint2 fwd2[2][31 * 32];  // per-lane pass-2 forward zetas [k][lane]
+  uint2 inv1[2][31 * 32];  // per-lane pass-1 inverse zetas [k][lane]
+};
+
+
+
+enum : uint32_t {
+  kGateAnd = 0, kGateNand, kGateOr, kGateNor, kGateXor, kGateXnor,
+  kGateNot, kGateMux, kGateCopy, kGateConst0, kGateConst1, kGateTypes
+};
+
+constexpr unsigned int kDevTimeout = 1u;
+
+// One blind rotation: input = cst + sa * W[ia] + sb * W[ib] (LWE_n, Torus32).
+struct BrJob {
+  uint32_t ia, ib, cst;
+  int16_t sa, sb;
+};
+static_assert(sizeof(BrJob) == 16, "BrJob layout");
+
+struct BrArgs {
+  const uint32_t *bsk;    // NTT-domain key: [n][6] rows of [c_out 2][prime 2][N] (per-lane order)
+  const uint32_t *wires;  // [*][632] LWE_n ciphertexts
+  const BrJob *jobs;
+  int num_jobs;
+  int n;
+  uint32_t *out;          // [num_jobs][1028] extracted LWE_N samples
+  const TwiddleGlobal *tg;
+  unsigned int *status;   // device status word (kDevTimeout on a watchdog expiry)
+  TwiddleConst tc;        // warp-uniform twiddles, read from the parameter bank
+};
+
+// One gate output.  Bootstrapped gates key-switch br_out[j0] (+ br_out[j1] + 1/8
+// for MUX); NOT / COPY read wire ia; CONST writes a trivial sample.
+struct KsJob {
+  uint32_t type, j0, j1, ia, out;
+};
+
+struct KsArgs {
+  const uint32_t *ksk;     // [N][8][3][632] rows for digits 1..3
+  const uint32_t *br_out;  // [*][1028]
+  const uint32_t *wires;   // [*][632]
+  const KsJob *jobs;
+  int n;
+  uint32_t *out;           // destination rows (out_stride words apart)
+  int out_stride;
+};
+
+struct BrShape {
+  int H;   // row groups per prime: 2H warps per gate
+  int GT;  // gates per CTA
+};
+
+// Twiddle tables for the two CRT primes (computed on the host, once).
+void make_twiddles(TwiddleConst *tc, TwiddleGlobal *tg);
+
+cudaError_t launch_bsk_to_ntt(const uint32_t *bsk_coef, int n, uint32_t *bsk_ntt, const TwiddleConst &tc,
+                              const TwiddleGlobal *tg, cudaStream_t st);
+size_t br_smem(BrShape s);
+int br_threads(BrShape s);
+bool br_shape_supported(BrShape s);
+int br_occupancy(BrShape s);  // resident CTAs per SM (0: cannot launch)
+cudaError_t launch_br(const BrArgs &args, BrShape s, int grid, cudaStream_t st);
+cudaError_t launch_ks(const KsArgs &args, int num_jobs, cudaStream_t st);
+cudaError_t launch_gather(const uint32_t *wires, const uint32_t *idx, int count, int n, uint32_t *dst,
+                          int dst_stride, cudaStream_t st);
+
+// per-shape launchers (one translation unit per H)
+cudaError_t launch_br_h1(const BrArgs &args, int GT, int grid, cudaStream_t st);
+cudaError_t launch_br_h2(const BrArgs &args, int GT, int grid, cudaStream_t st);
+cudaError_t launch_br_h3(const BrArgs &args, int GT, int grid, cudaStream_t st);
+cudaError_t launch_br_h6(const BrArgs &args, int GT, int grid, cudaStream_t st);
+
+}  // namespace arx

@@ -1,0 +1,30 @@
+// br_h3.cu -- blind-rotation kernel shapes with H = 3 (2H warps per gate).
+#include "br_kernel.cuh"
+
+namespace arx {
+
+cudaError_t launch_br_h3(const BrArgs &args, int GT, int grid, cudaStream_t st) {
+  switch (GT) {
+    case 1: return br::launch_shape<3, 1>(args, grid, st);
+    case 2: return br::launch_shape<3, 2>(args, grid, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+size_t br_smem_h3(int GT) {
+  switch (GT) {
+    case 1: return br::br_smem_bytes<3, 1>();
+    case 2: return br::br_smem_bytes<3, 2>();
+    default: return 0;
+  }
+}
+
+int br_occupancy_h3(int GT) {
+  switch (GT) {
+    case 1: return br::occupancy_shape<3, 1>();
+    case 2: return br::occupancy_shape<3, 2>();
+    default: return 0;
+  }
+}
+
+}  // namespace arx

@@ -1,0 +1,27 @@
+// br_h6.cu -- blind-rotation kernel shapes with H = 6 (2H warps per gate).
+#include "br_kernel.cuh"
+
+namespace arx {
+
+cudaError_t launch_br_h6(const BrArgs &args, int GT, int grid, cudaStream_t st) {
+  switch (GT) {
+    case 1: return br::launch_shape<6, 1>(args, grid, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+size_t br_smem_h6(int GT) {
+  switch (GT) {
+    case 1: return br::br_smem_bytes<6, 1>();
+    default: return 0;
+  }
+}
+
+int br_occupancy_h6(int GT) {
+  switch (GT) {
+    case 1: return br::occupancy_shape<6, 1>();
+    default: return 0;
+  }
+}
+
+}  // namespace arx

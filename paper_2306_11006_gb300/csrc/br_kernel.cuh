@@ -1,0 +1,435 @@
+// br_kernel.cuh -- the blind-rotation kernel of CGGI gate bootstrapping on GB300.
+//
+//   br_kernel<H, GT>: gate pre-combination, mod switch, blind rotation through n
+//   CMux external products, sample extraction (Fig. 2 and Sec. 2.2 of the paper).
+//   Each br_h*.cu translation unit instantiates the shapes of one H.
+//
+// Blind rotation kernel organisation.  A gate is processed by 2H consumer warps:
+// warp (P, h) carries prime P of the CRT pair and the h-th group of 6/H TGSW rows.
+// GT gates share a CTA so that every bootstrapping-key row (16 KiB: two output
+// polynomials x two primes) is brought into shared memory once per CTA by a
+// producer warp (cp.async.bulk into a 4-stage mbarrier ring) and read by all
+// 2 GT warps that use it.  Every wait is bounded: on a timeout the kernel records
+// kDevTimeout in the device status word, stops waiting, runs to the end and returns.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "arx_device.cuh"
+
+namespace arx {
+namespace br {
+
+constexpr uint32_t pow_mod(uint64_t b, uint64_t e, uint64_t m) {
+  uint64_t r = 1;
+  b %= m;
+  while (e) {
+    if (e & 1) r = r * b % m;
+    b = b * b % m;
+    e >>= 1;
+  }
+  return (uint32_t)r;
+}
+constexpr uint32_t kQ0InvQ1 = pow_mod(kQ0, kQ1 - 2, kQ1);
+constexpr uint32_t kQ0InvQ1Shoup = (uint32_t)(((uint64_t)kQ0InvQ1 << 32) / kQ1);
+constexpr uint64_t kM = (uint64_t)kQ0 * kQ1;
+static_assert(kQ0InvQ1 == 39018686u, "CRT constant");
+static_assert(22ull * kQ0 < (1ull << 32) && 22ull * kQ1 < (1ull << 32), "lazy forward bound");
+static_assert(6ull * 1024 * 64 * (1ull << 31) * 2 < kM, "CRT range must hold the exact products");
+
+// Gadget decomposition offset: 2^10 rounds to the top 21 bits, 64 * 2^(32-7p)
+// recentres each 7-bit digit into [-64, 64).
+constexpr uint32_t kDecOffset = (1u << 10) + (64u << 25) + (64u << 18) + (64u << 11);
+
+constexpr long long kWaitCycles = 4000000000ll;  // ~2 s at GB300 clocks
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait; returns false (and flags the CTA and the device status) on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
+                                          unsigned int *status) {
+  if (*abort_flag) return false;
+  if (mbar_try_wait(bar, parity)) return true;
+  long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (*abort_flag) return false;
+    if (clock64() - t0 > kWaitCycles) {
+      *abort_flag = 1;
+      atomicOr(status, kDevTimeout);
+      return false;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void named_bar(int id, int threads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
+}
+
+__device__ __forceinline__ uint32_t modswitch(uint32_t x) { return (x + (1u << 20)) >> 21; }
+
+// (x0 mod q0, x1 mod q1), both fully reduced -> centred integer mod 2^32.
+__device__ __forceinline__ uint32_t crt_torus(uint32_t x0, uint32_t x1) {
+  uint32_t d = x1 + 2u * kQ1 - x0;
+  uint32_t k = csub(shoup_mul<1>(kQ0InvQ1, kQ0InvQ1Shoup, d), kQ1);
+  uint64_t X = (uint64_t)kQ0 * k + x0;
+  uint32_t r = (uint32_t)X;
+  return X > kM / 2 ? r - (uint32_t)kM : r;
+}
+
+template <int P>
+__device__ __forceinline__ uint32_t red12(uint32_t x) {  // [0, 12q) -> [0, 2q)
+  x = csub(x, 8u * Prime<P>::q);
+  x = csub(x, 4u * Prime<P>::q);
+  return csub(x, 2u * Prime<P>::q);
+}
+
+// Gadget digits of temp = X^a ACC - ACC for both polynomials, computed by the
+// gate's threads into dig[c][k] and packed as three biased 7-bit fields
+// (digit + 64), p = 1 in the low byte.
+template <int kGateThreads>
+__device__ __forceinline__ void make_digits(uint32_t *dig, const uint32_t *A, uint32_t a, int tid_g) {
+#pragma unroll 4
+  for (int idx = tid_g; idx < 2 * kN; idx += kGateThreads) {
+    const uint32_t c = (uint32_t)idx >> 10, k = (uint32_t)idx & 1023u;
+    const uint32_t *P = A + c * kN;
+    const uint32_t j = (k - a) & 2047u;
+    uint32_t v = P[j & 1023u];
+    v = (j & 1024u) ? 0u - v : v;
+    const uint32_t y = v - P[k] + kDecOffset;
+    dig[idx] = (y >> 25) | (((y >> 18) & 0x7Fu) << 8) | (((y >> 11) & 0x7Fu) << 16);
+  }
+}
+
+struct BrShared {
+  uint32_t *ring;     // kStages x kChunkWords
+  uint32_t *acc;      // GT x [2][N]
+  uint32_t *dig;      // GT x [2][N] packed gadget digits
+  uint32_t *scratch;  // consumer warps x kScratch
+  uint16_t *abar;     // GT x kAbarPitch
+  uint64_t *full, *empty;
+  volatile int *abort_flag;
+};
+
+constexpr int kStages = 4;
+constexpr int kAbarPitch = 640;
+
+template <int H>
+__host__ __device__ constexpr int scratch_words() { return (H == 1 ? 1 : 2) * kXpose; }
+
+template <int H, int GT>
+constexpr size_t br_smem_bytes() {
+  return (size_t)kStages * kChunkBytes + (size_t)GT * 4 * kN * 4 +
+         (size_t)2 * H * GT * scratch_words<H>() * 4 + (size_t)GT * kAbarPitch * 2 + 2 * kStages * 8 + 16;
+}
+
+template <int H, int GT>
+__device__ __forceinline__ BrShared br_carve(uint8_t *smem) {
+  BrShared s;
+  s.ring = reinterpret_cast<uint32_t *>(smem);
+  s.acc = s.ring + kStages * kChunkWords;
+  s.dig = s.acc + GT * 2 * kN;
+  s.scratch = s.dig + GT * 2 * kN;
+  s.abar = reinterpret_cast<uint16_t *>(s.scratch + 2 * H * GT * scratch_words<H>());
+  s.full = reinterpret_cast<uint64_t *>(s.abar + GT * kAbarPitch);
+  s.empty = s.full + kStages;
+  s.abort_flag = reinterpret_cast<volatile int *>(s.empty + kStages);
+  return s;
+}
+
+// One consumer warp (prime P, row group h) over all tiles of the launch.
+template <int P, int H, int GT>
+__device__ __forceinline__ void br_consumer(const BrShared &S, const BrArgs &args, int g, int h, int lane) {
+  constexpr int kRpg = 6 / H;
+  constexpr int kScr = scratch_words<H>();
+  constexpr int kGateThreads = 64 * H;
+  const int n = args.n;
+  const int bar_id = 1 + g;
+  const int role = h * 2 + P;
+  const int wbase = g * 2 * H;  // first warp of this gate
+  const int tid_g = role * 32 + lane;
+  uint32_t *A = S.acc + g * 2 * kN;
+  uint32_t *D = S.dig + g * 2 * kN;
+  uint16_t *abar = S.abar + g * kAbarPitch;
+  uint32_t *myscr = S.scratch + (wbase + role) * kScr;
+  const uint2 *tw2 = args.tg->fwd2[P];
+  const uint2 *tw1 = args.tg->inv1[P];
+  const int tiles = (args.num_jobs + GT - 1) / GT;
+  uint32_t it = 0;
+
+  for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++it) {
+    const int job_idx = tile * GT + g;
+    const bool active = job_idx < args.num_jobs;
+    const BrJob jb = args.jobs[active ? job_idx : args.num_jobs - 1];
+    const uint32_t *wa = args.wires + (size_t)jb.ia * kWireStride;
+    const uint32_t *wb = args.wires + (size_t)jb.ib * kWireStride;
+    const uint32_t sa = (uint32_t)(int32_t)jb.sa, sb = (uint32_t)(int32_t)jb.sb;
+    // Fig. 2 top box: linear pre-combination, then the mod switch to Z_2N.
+    for (int k = tid_g; k < n; k += kGateThreads) abar[k] = (uint16_t)modswitch(sa * wa[k] + sb * wb[k]);
+    const uint32_t bbar = modswitch(jb.cst + sa * wa[n] + sb * wb[n]);
+    // ACC = X^-bbar (0, testv), testv = mu (1 + X + ... + X^(N-1)).
+    const uint32_t shift = (2u * kN - bbar) & (2u * kN - 1);
+    for (int k = tid_g; k < 2 * kN; k += kGateThreads) {
+      uint32_t v = 0;
+      if (k >= kN) v = (((uint32_t)(k - kN) - shift) & (2u * kN - 1)) < (uint32_t)kN ? kMu : 0u - kMu;
+      A[k] = v;
+    }
+    named_bar(bar_id, kGateThreads);
+
+    for (int i = 0; i < n; ++i) {
+      make_digits<kGateThreads>(D, A, abar[i], tid_g);
+      named_bar(bar_id, kGateThreads);  // B0: digits ready
+      uint32_t acc0[32], acc1[32];
+#pragma unroll
+      for (int e = 0; e < 32; ++e) acc0[e] = acc1[e] = 0;
+#pragma unroll 1
+      for (int rr = 0; rr < kRpg; ++rr) {
+        const int r = h * kRpg + rr;
+        const int c = r / 3, p = r - 3 * (r / 3);
+        const uint32_t *dc = D + c * kN;
+        uint32_t x[32];
+        const int sh = 8 * p;
+#pragma unroll
+        for (int e = 0; e < 32; ++e) x[e] = ((dc[lane + 32 * e] >> sh) & 0x7Fu) + (Prime<P>::q - 64u);
+        ntt_fwd<P>(x, myscr, args.tc, tw2, lane);
+        // MAC with the NTT-domain key row staged in the ring.
+        const uint32_t jc = (it * (uint32_t)n + (uint32_t)i) * 6u + (uint32_t)r;
+        const uint32_t slot = jc % kStages;
+        mbar_wait(S.full + slot, (jc / kStages) & 1u, S.abort_flag, args.status);
+        const uint4 *B0 = reinterpret_cast<const uint4 *>(S.ring + slot * kChunkWords + (0 * 2 + P) * kN);
+        const uint4 *B1 = reinterpret_cast<const uint4 *>(S.ring + slot * kChunkWords + (1 * 2 + P) * kN);
+#pragma unroll
+        for (int e4 = 0; e4 < 8; ++e4) {
+          const uint4 b0 = B0[e4 * 32 + lane];
+          const uint4 b1 = B1[e4 * 32 + lane];
+          acc0[4 * e4 + 0] += mont_mul<P>(x[4 * e4 + 0], b0.x);
+          acc0[4 * e4 + 1] += mont_mul<P>(x[4 * e4 + 1], b0.y);
+          acc0[4 * e4 + 2] += mont_mul<P>(x[4 * e4 + 2], b0.z);
+          acc0[4 * e4 + 3] += mont_mul<P>(x[4 * e4 + 3], b0.w);
+          acc1[4 * e4 + 0] += mont_mul<P>(x[4 * e4 + 0], b1.x);
+          acc1[4 * e4 + 1] += mont_mul<P>(x[4 * e4 + 1], b1.y);
+          acc1[4 * e4 + 2] += mont_mul<P>(x[4 * e4 + 2], b1.z);
+          acc1[4 * e4 + 3] += mont_mul<P>(x[4 * e4 + 3], b1.w);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(S.empty + slot);
+      }
+
+      const int mb = 16 * P, ob = 16 * (1 - P);
+      if constexpr (H == 1) {
+#pragma unroll
+        for (int e = 0; e < 32; ++e) {
+          acc0[e] = red12<P>(acc0[e]);
+          acc1[e] = red12<P>(acc1[e]);
+        }
+        ntt_inv<P>(acc0, myscr, args.tc, tw1, lane);
+        ntt_inv<P>(acc1, myscr, args.tc, tw1, lane);
+        __syncwarp();
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          myscr[e * 32 + lane] = csub(acc0[ob + e], Prime<P>::q);
+          myscr[512 + e * 32 + lane] = csub(acc1[ob + e], Prime<P>::q);
+        }
+        named_bar(bar_id, kGateThreads);  // B2: CRT halves posted
+        const uint32_t *peer = S.scratch + (wbase + (1 - P)) * kScr;
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          const uint32_t m0 = csub(acc0[mb + e], Prime<P>::q), m1 = csub(acc1[mb + e], Prime<P>::q);
+          const uint32_t o0 = peer[e * 32 + lane], o1 = peer[512 + e * 32 + lane];
+          const uint32_t r0 = P == 0 ? crt_torus(m0, o0) : crt_torus(o0, m0);
+          const uint32_t r1 = P == 0 ? crt_torus(m1, o1) : crt_torus(o1, m1);
+          A[lane + 32 * (mb + e)] += r0;
+          A[kN + lane + 32 * (mb + e)] += r1;
+        }
+        named_bar(bar_id, kGateThreads);  // B3: ACC updated
+      } else {
+        // reduce partial sums over the H row groups into the owner warp (P, c)
+        if (h != 0) {
+          __syncwarp();
+#pragma unroll
+          for (int e = 0; e < 32; ++e) myscr[e * 32 + lane] = acc0[e];
+        }
+        if (h != 1) {
+          __syncwarp();
+#pragma unroll
+          for (int e = 0; e < 32; ++e) myscr[kXpose + e * 32 + lane] = acc1[e];
+        }
+        named_bar(bar_id, kGateThreads);  // B1: partials posted
+        if (h < 2) {
+          uint32_t *half = myscr + h * kXpose;
+          if (h == 0) {
+            for (int hp = 1; hp < H; ++hp) {
+              const uint32_t *src = S.scratch + (wbase + hp * 2 + P) * kScr;
+#pragma unroll
+              for (int e = 0; e < 32; ++e) acc0[e] += src[e * 32 + lane];
+            }
+#pragma unroll
+            for (int e = 0; e < 32; ++e) acc0[e] = red12<P>(acc0[e]);
+            ntt_inv<P>(acc0, half, args.tc, tw1, lane);
+            __syncwarp();
+#pragma unroll
+            for (int e = 0; e < 16; ++e) half[e * 32 + lane] = csub(acc0[ob + e], Prime<P>::q);
+          } else {
+            for (int hp = 0; hp < H; ++hp) {
+              if (hp == 1) continue;
+              const uint32_t *src = S.scratch + (wbase + hp * 2 + P) * kScr + kXpose;
+#pragma unroll
+              for (int e = 0; e < 32; ++e) acc1[e] += src[e * 32 + lane];
+            }
+#pragma unroll
+            for (int e = 0; e < 32; ++e) acc1[e] = red12<P>(acc1[e]);
+            ntt_inv<P>(acc1, half, args.tc, tw1, lane);
+            __syncwarp();
+#pragma unroll
+            for (int e = 0; e < 16; ++e) half[e * 32 + lane] = csub(acc1[ob + e], Prime<P>::q);
+          }
+        }
+        named_bar(bar_id, kGateThreads);  // B2: CRT halves posted
+        if (h < 2) {
+          const int c = h;
+          const uint32_t *peer = S.scratch + (wbase + c * 2 + (1 - P)) * kScr + c * kXpose;
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            const uint32_t m = csub(c == 0 ? acc0[mb + e] : acc1[mb + e], Prime<P>::q);
+            const uint32_t o = peer[e * 32 + lane];
+            A[c * kN + lane + 32 * (mb + e)] += P == 0 ? crt_torus(m, o) : crt_torus(o, m);
+          }
+        }
+        named_bar(bar_id, kGateThreads);  // B3: ACC updated
+      }
+    }
+
+    // Sample extraction of coefficient 0: a'_0 = a_0, a'_j = -a_(N-j), b' = b_0.
+    if (active) {
+      uint32_t *o = args.out + (size_t)job_idx * kOutStride;
+      for (int k = tid_g; k <= kN; k += kGateThreads)
+        o[k] = k == 0 ? A[0] : (k < kN ? 0u - A[kN - k] : A[kN]);
+    }
+    named_bar(bar_id, kGateThreads);
+  }
+}
+
+template <int H, int GT>
+__global__ void __launch_bounds__((2 * H * GT + 1) * 32, 1) br_kernel(const __grid_constant__ BrArgs args) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  BrShared S = br_carve<H, GT>(smem);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int kCons = 2 * H * GT;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(S.full + s, 1);
+      mbar_init(S.empty + s, 2 * GT);
+    }
+    *S.abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (args.num_jobs <= 0) return;
+
+  if (warp == kCons) {  // producer: stream BSK rows into the ring
+    if (lane == 0) {
+      const int tiles = (args.num_jobs + GT - 1) / GT;
+      uint32_t jc = 0;
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
+        for (int i = 0; i < args.n && ok; ++i) {
+          for (int r = 0; r < 6; ++r, ++jc) {
+            const uint32_t slot = jc % kStages;
+            if (jc >= (uint32_t)kStages && !mbar_wait(S.empty + slot, ((jc / kStages) - 1) & 1u, S.abort_flag, args.status)) {
+              ok = false;
+              break;
+            }
+            mbar_expect_tx(S.full + slot, kChunkBytes);
+            bulk_g2s(S.ring + slot * kChunkWords, args.bsk + ((size_t)i * 6 + r) * kChunkWords, kChunkBytes,
+                     S.full + slot);
+          }
+        }
+      }
+      if (!ok) {  // drain copies still in flight (bounded) before the CTA retires
+        for (uint32_t k = jc > (uint32_t)kStages ? jc - kStages : 0; k < jc; ++k) {
+          long long t0 = clock64();
+          while (!mbar_try_wait(S.full + (k % kStages), (k / kStages) & 1u) && clock64() - t0 < kWaitCycles) {
+          }
+        }
+      }
+    }
+    return;
+  }
+  const int g = warp / (2 * H), role = warp % (2 * H);
+  const int P = role & 1, h = role >> 1;
+  if (P == 0)
+    br_consumer<0, H, GT>(S, args, g, h, lane);
+  else
+    br_consumer<1, H, GT>(S, args, g, h, lane);
+}
+
+template <int H, int GT>
+cudaError_t prepare_shape() {
+  static bool done = false;  // calls are serialised by the engine lock
+  if (done) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(br_kernel<H, GT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)br_smem_bytes<H, GT>());
+  if (e == cudaSuccess) done = true;
+  return e;
+}
+
+template <int H, int GT>
+cudaError_t launch_shape(const BrArgs &args, int grid, cudaStream_t st) {
+  cudaError_t e = prepare_shape<H, GT>();
+  if (e != cudaSuccess) return e;
+  br_kernel<H, GT><<<grid, (2 * H * GT + 1) * 32, br_smem_bytes<H, GT>(), st>>>(args);
+  return cudaGetLastError();
+}
+
+// Resident CTAs per SM of a shape (0 if it cannot launch on this device).
+template <int H, int GT>
+int occupancy_shape() {
+  if (prepare_shape<H, GT>() != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  int blocks = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, br_kernel<H, GT>, (2 * H * GT + 1) * 32,
+                                                    br_smem_bytes<H, GT>()) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return blocks;
+}
+
+}  // namespace br
+}  // namespace arx

@@ -1,0 +1,874 @@
+// engine.cpp -- host side of libarx: device state, key sets, workspaces, the wave
+// scheduler for netlists, plans with CUDA-graph replay, the launch-shape
+// autotuner, and the C-ABI entry points declared in include/arx.h.
+//
+// Runtime structure follows Sec. 4.2 / Sec. 5 of the paper, re-designed for one
+// GB300: the netlist is levelized once into waves (FIFO topological sort); each
+// wave becomes one blind-rotation launch over all of its bootstrapped gates (of any
+// gate type, with a per-gate descriptor) and one key-switch launch; wires stay in
+// HBM for the whole evaluation (instead of pinned host memory); the per-wave
+// descriptor arrays are built on the host ahead of time and stay on the device
+// (instead of per-stream buffers filled by host callbacks); waves are ordered by
+// stream order, or replayed as a single CUDA graph (instead of event fences).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/arx.h"
+#include "arx_kernels.h"
+#include "engine_internal.h"
+
+namespace arx {
+
+thread_local std::string t_err;
+
+int fail(int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  t_err = buf;
+  return code;
+}
+
+#define CK(call)                                                                            \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess) {                                                                \
+      return fail(e_ == cudaErrorMemoryAllocation ? ARX_ENOMEM : ARX_ECUDA, "%s: %s", #call, \
+                  cudaGetErrorString(e_));                                                  \
+    }                                                                                       \
+  } while (0)
+
+cudaError_t DevBuf::reserve(size_t bytes) {
+  if (bytes <= cap) return cudaSuccess;
+  if (p) cudaFree(p);
+  p = nullptr;
+  cap = 0;
+  size_t want = bytes + bytes / 4;  // grow with headroom
+  cudaError_t e = cudaMalloc(&p, want);
+  if (e == cudaSuccess) cap = want;
+  return e;
+}
+
+void DevBuf::release() {
+  if (p) cudaFree(p);
+  p = nullptr;
+  cap = 0;
+}
+
+Engine &eng() {
+  static Engine *e = new Engine;  // intentionally never destroyed (no teardown after the CUDA runtime)
+  return *e;
+}
+
+int ensure_init(Engine &E) {
+  if (E.ready) return ARX_OK;
+  CK(cudaGetDevice(&E.device));
+  cudaDeviceProp prop;
+  CK(cudaGetDeviceProperties(&prop, E.device));
+  if (prop.major < 10)
+    return fail(ARX_ECUDA, "device %s (sm_%d%d): libarx is built for sm_103a", prop.name, prop.major, prop.minor);
+  E.sms = prop.multiProcessorCount;
+  E.smem_optin = prop.sharedMemPerBlockOptin;
+  std::unique_ptr<TwiddleGlobal> tg(new TwiddleGlobal);
+  make_twiddles(&E.tc, tg.get());
+  CK(cudaMalloc(&E.tg, sizeof(TwiddleGlobal)));
+  CK(cudaMemcpy(E.tg, tg.get(), sizeof(TwiddleGlobal), cudaMemcpyHostToDevice));
+  CK(cudaMalloc(&E.status, sizeof(unsigned int)));
+  CK(cudaMemset(E.status, 0, sizeof(unsigned int)));
+  CK(cudaStreamCreateWithFlags(&E.stream, cudaStreamNonBlocking));
+  E.ready = true;
+  return ARX_OK;
+}
+
+bool is_device_ptr(const void *p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int resolve_keyset(Engine &E, int keyset, Keyset **out) {
+  if (keyset < 0) keyset = E.last;
+  if (keyset < 0 || keyset >= (int)E.keysets.size() || !E.keysets[keyset].used)
+    return fail(ARX_ENOKEYS, "no key set %d loaded", keyset);
+  *out = &E.keysets[keyset];
+  return ARX_OK;
+}
+
+int read_status(Engine &E, cudaStream_t st) {
+  unsigned int v = 0;
+  CK(cudaMemcpyAsync(&v, E.status, sizeof(v), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (v) {
+    CK(cudaMemsetAsync(E.status, 0, sizeof(unsigned int), st));
+    CK(cudaStreamSynchronize(st));
+    return fail(ARX_ETIMEOUT, "device watchdog expired (status 0x%x)", v);
+  }
+  return ARX_OK;
+}
+
+// --------------------------------------------------------------------------
+// gate linear parts (Fig. 2 top box; constants as in the design notes)
+// --------------------------------------------------------------------------
+bool gate_linear(uint32_t type, int16_t *sa, int16_t *sb, uint32_t *cst) {
+  const uint32_t e = ARX_MU, q = 2u * ARX_MU;
+  switch (type) {
+    case ARX_AND: *sa = 1; *sb = 1; *cst = 0u - e; return true;
+    case ARX_NAND: *sa = -1; *sb = -1; *cst = e; return true;
+    case ARX_OR: *sa = 1; *sb = 1; *cst = e; return true;
+    case ARX_NOR: *sa = -1; *sb = -1; *cst = 0u - e; return true;
+    case ARX_XOR: *sa = 2; *sb = 2; *cst = q; return true;
+    case ARX_XNOR: *sa = -2; *sb = -2; *cst = 0u - q; return true;
+    default: return false;
+  }
+}
+
+int gate_arity(uint32_t type) {
+  switch (type) {
+    case ARX_NOT: case ARX_COPY: return 1;
+    case ARX_CONST0: case ARX_CONST1: return 0;
+    case ARX_MUX: return 3;
+    default: return 2;
+  }
+}
+
+// Appends the blind-rotation jobs and the key-switch job of one gate.
+void emit_gate(uint32_t type, uint32_t w0, uint32_t w1, uint32_t w2, uint32_t out, std::vector<BrJob> &br,
+               std::vector<KsJob> &ks, uint32_t br_base) {
+  KsJob k{type, 0, 0, w0, out};
+  BrJob j{};
+  if (type == ARX_MUX) {
+    // MUX(s, t, f): AND(s, t) and AND(not s, f) blind-rotated, summed with 1/8, one KS.
+    j = BrJob{w0, w1, 0u - ARX_MU, 1, 1};
+    k.j0 = (uint32_t)br.size() - br_base;
+    br.push_back(j);
+    j = BrJob{w0, w2, 0u - ARX_MU, -1, 1};
+    k.j1 = (uint32_t)br.size() - br_base;
+    br.push_back(j);
+  } else if (gate_linear(type, &j.sa, &j.sb, &j.cst)) {
+    j.ia = w0;
+    j.ib = w1;
+    k.j0 = (uint32_t)br.size() - br_base;
+    br.push_back(j);
+  }
+  ks.push_back(k);
+}
+
+// --------------------------------------------------------------------------
+// launch shapes: heuristic and autotuned
+// --------------------------------------------------------------------------
+const BrShape kShapes[] = {{6, 1}, {3, 1}, {3, 2}, {2, 1}, {2, 3}, {1, 1}, {1, 2}, {1, 4}, {1, 6}};
+
+int ctas_per_sm(Engine &E, BrShape s) {
+  for (auto &kv : E.occ)
+    if (kv.first.H == s.H && kv.first.GT == s.GT) return kv.second;
+  const int occ = br_occupancy(s);
+  E.occ.push_back({s, occ});
+  return occ;
+}
+
+// Plain mode: about twelve consumer warps per SM, more gates per CTA as the wave widens.
+BrShape heuristic_shape(Engine &E, int jobs) {
+  if (E.forced.H) return E.forced;
+  const int per_sm = (jobs + E.sms - 1) / E.sms;
+  if (per_sm <= 1) return {6, 1};
+  if (per_sm == 2) return {3, 2};
+  if (per_sm == 3) return {2, 3};
+  if (per_sm <= 4) return {1, 4};
+  return {1, 6};
+}
+
+int grid_for(Engine &E, BrShape s, int jobs) {
+  const int tiles = (jobs + s.GT - 1) / s.GT;
+  const int cap = E.sms * std::max(1, ctas_per_sm(E, s));
+  return std::max(1, std::min(tiles, cap));
+}
+
+// Autotuner: time one full wave of every shape once per (device, n) with a short
+// synthetic blind rotation (timing is data-independent), then pick the shape
+// minimising waves x time-per-wave for each launch width.
+int calibrate(Engine &E, int n) {
+  if (E.tuned_n == n) return ARX_OK;
+  const int ncal = std::min(n, 16);
+  int max_jobs = 0;
+  for (BrShape s : kShapes) max_jobs = std::max(max_jobs, E.sms * s.GT * std::max(1, ctas_per_sm(E, s)));
+  DevBuf bsk, wires, jobs, out;
+  CK(bsk.reserve((size_t)ncal * 6 * kChunkBytes));
+  CK(wires.reserve((size_t)kWireStride * 4 * 2));
+  CK(jobs.reserve(sizeof(BrJob) * max_jobs));
+  CK(out.reserve((size_t)kOutStride * 4 * max_jobs));
+  CK(cudaMemset(bsk.p, 0, (size_t)ncal * 6 * kChunkBytes));
+  CK(cudaMemset(wires.p, 0, (size_t)kWireStride * 4 * 2));
+  std::vector<BrJob> hj(max_jobs, BrJob{0, 1, ARX_MU, 1, 1});
+  CK(cudaMemcpy(jobs.p, hj.data(), sizeof(BrJob) * max_jobs, cudaMemcpyHostToDevice));
+  cudaEvent_t a, b;
+  CK(cudaEventCreate(&a));
+  CK(cudaEventCreate(&b));
+  E.tune.clear();
+  for (BrShape s : kShapes) {
+    if (!ctas_per_sm(E, s)) continue;
+    BrArgs args{};
+    args.bsk = bsk.as<uint32_t>();
+    args.wires = wires.as<uint32_t>();
+    args.jobs = jobs.as<BrJob>();
+    args.num_jobs = E.sms * s.GT * ctas_per_sm(E, s);
+    args.n = ncal;
+    args.out = out.as<uint32_t>();
+    args.tg = E.tg;
+    args.status = E.status;
+    args.tc = E.tc;
+    const int grid = grid_for(E, s, args.num_jobs);
+    float best = 1e30f;
+    for (int rep = 0; rep < 3; ++rep) {
+      CK(cudaEventRecord(a, E.stream));
+      CK(launch_br(args, s, grid, E.stream));
+      CK(cudaEventRecord(b, E.stream));
+      CK(cudaEventSynchronize(b));
+      float ms = 0;
+      CK(cudaEventElapsedTime(&ms, a, b));
+      if (rep) best = std::min(best, ms);
+    }
+    TuneEntry t;
+    t.shape = s;
+    t.wave_ms_per_cmux = best / ncal;
+    t.gates_per_wave = args.num_jobs;
+    E.tune.push_back(t);
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  bsk.release();
+  wires.release();
+  jobs.release();
+  out.release();
+  int rc = read_status(E, E.stream);
+  if (rc) return rc;
+  E.tuned_n = n;
+  return ARX_OK;
+}
+
+BrShape tuned_shape(Engine &E, int jobs, int n) {
+  if (E.forced.H) return E.forced;
+  if (E.tune.empty() || E.tuned_n != n) return heuristic_shape(E, jobs);
+  double best = 1e300;
+  BrShape pick = E.tune.front().shape;
+  for (const TuneEntry &t : E.tune) {
+    const int waves = (jobs + t.gates_per_wave - 1) / t.gates_per_wave;
+    const double cost = waves * t.wave_ms_per_cmux;
+    if (cost < best * 0.999) {
+      best = cost;
+      pick = t.shape;
+    }
+  }
+  return pick;
+}
+
+// --------------------------------------------------------------------------
+// levelization (Sec. 4.2): successor lists, predecessor counts, a FIFO of ready
+// gates; wave = 0 without gate inputs, else 1 + max wave of the gate inputs.
+// --------------------------------------------------------------------------
+int validate_netlist(const arx_netlist *nl) {
+  if (!nl) return fail(ARX_EINVAL, "null netlist");
+  if (nl->num_gates && (!nl->type || !nl->in0)) return fail(ARX_EINVAL, "netlist arrays missing");
+  if (nl->num_outputs && !nl->outputs) return fail(ARX_EINVAL, "netlist outputs missing");
+  const uint64_t wires = (uint64_t)nl->num_inputs + nl->num_gates;
+  for (uint32_t g = 0; g < nl->num_gates; ++g) {
+    const uint32_t t = nl->type[g];
+    if (t > ARX_CONST1) return fail(ARX_EINVAL, "gate %u: bad type %u", g, t);
+    const int ar = gate_arity(t);
+    if (ar >= 2 && !nl->in1) return fail(ARX_EINVAL, "netlist in1 missing");
+    if (ar >= 3 && !nl->in2) return fail(ARX_EINVAL, "netlist in2 missing");
+    const uint32_t *ins[3] = {nl->in0, nl->in1, nl->in2};
+    for (int s = 0; s < ar; ++s)
+      if (ins[s][g] >= wires) return fail(ARX_EINVAL, "gate %u input %d: wire %u out of range", g, s, ins[s][g]);
+  }
+  for (uint32_t o = 0; o < nl->num_outputs; ++o)
+    if (nl->outputs[o] >= wires) return fail(ARX_EINVAL, "output %u: wire %u out of range", o, nl->outputs[o]);
+  return ARX_OK;
+}
+
+int levelize(const arx_netlist *nl, uint32_t *wave, uint32_t *depth) {
+  int rc = validate_netlist(nl);
+  if (rc) return rc;
+  const uint32_t G = nl->num_gates, I = nl->num_inputs;
+  const uint32_t *ins[3] = {nl->in0, nl->in1, nl->in2};
+  std::vector<uint32_t> npred(G, 0), start(G + 1, 0);
+  for (uint32_t g = 0; g < G; ++g)
+    for (int s = 0; s < gate_arity(nl->type[g]); ++s)
+      if (ins[s][g] >= I) {
+        npred[g]++;
+        start[ins[s][g] - I + 1]++;
+      }
+  for (uint32_t g = 0; g < G; ++g) start[g + 1] += start[g];
+  std::vector<uint32_t> succ(start[G]), fill(start.begin(), start.end() - 1);
+  for (uint32_t g = 0; g < G; ++g)
+    for (int s = 0; s < gate_arity(nl->type[g]); ++s)
+      if (ins[s][g] >= I) succ[fill[ins[s][g] - I]++] = g;
+  std::vector<uint32_t> fifo;
+  fifo.reserve(G);
+  for (uint32_t g = 0; g < G; ++g)
+    if (!npred[g]) fifo.push_back(g);
+  uint32_t d = 0;
+  for (size_t head = 0; head < fifo.size(); ++head) {
+    const uint32_t g = fifo[head];
+    uint32_t w = 0;
+    for (int s = 0; s < gate_arity(nl->type[g]); ++s)
+      if (ins[s][g] >= I) w = std::max(w, wave[ins[s][g] - I] + 1);
+    wave[g] = w;
+    d = std::max(d, w + 1);
+    for (uint32_t e = start[g]; e < start[g + 1]; ++e)
+      if (--npred[succ[e]] == 0) fifo.push_back(succ[e]);
+  }
+  if (fifo.size() != G) return fail(ARX_ECYCLE, "netlist has a cycle (%zu of %u gates ordered)", fifo.size(), G);
+  if (depth) *depth = d;
+  return ARX_OK;
+}
+
+// --------------------------------------------------------------------------
+// plans
+// --------------------------------------------------------------------------
+int plan_build(Engine &E, const arx_netlist *nl, int keyset, int mode, std::unique_ptr<Plan> &out) {
+  Keyset *ks = nullptr;
+  int rc = resolve_keyset(E, keyset, &ks);
+  if (rc) return rc;
+  std::vector<uint32_t> wave(nl->num_gates ? nl->num_gates : 1);
+  uint32_t depth = 0;
+  rc = levelize(nl, wave.data(), &depth);
+  if (rc) return rc;
+  std::unique_ptr<Plan> P(new Plan);
+  P->keyset = keyset < 0 ? E.last : keyset;
+  P->n = ks->n;
+  P->mode = mode;
+  P->num_inputs = nl->num_inputs;
+  P->num_gates = nl->num_gates;
+  P->outputs.assign(nl->outputs, nl->outputs + nl->num_outputs);
+  // bucket gates by wave, keeping gate order inside a wave
+  std::vector<uint32_t> cnt(depth + 1, 0), order(nl->num_gates);
+  for (uint32_t g = 0; g < nl->num_gates; ++g) cnt[wave[g] + 1]++;
+  for (uint32_t w = 0; w < depth; ++w) cnt[w + 1] += cnt[w];
+  std::vector<uint32_t> pos(cnt.begin(), cnt.end() - 1);
+  for (uint32_t g = 0; g < nl->num_gates; ++g) order[pos[wave[g]]++] = g;
+  std::vector<BrJob> br;
+  std::vector<KsJob> ksj;
+  int max_br = 0;
+  for (uint32_t w = 0; w < depth; ++w) {
+    Level L{};
+    L.br_off = (int)br.size();
+    L.ks_off = (int)ksj.size();
+    for (uint32_t k = cnt[w]; k < cnt[w + 1]; ++k) {
+      const uint32_t g = order[k];
+      const uint32_t t = nl->type[g];
+      const int ar = gate_arity(t);
+      emit_gate(t, ar > 0 ? nl->in0[g] : 0, ar > 1 ? nl->in1[g] : 0, ar > 2 ? nl->in2[g] : 0,
+                nl->num_inputs + g, br, ksj, (uint32_t)L.br_off);
+    }
+    L.br_cnt = (int)br.size() - L.br_off;
+    L.ks_cnt = (int)ksj.size() - L.ks_off;
+    max_br = std::max(max_br, L.br_cnt);
+    P->levels.push_back(L);
+  }
+  P->bootstraps = br.size();
+  if (mode == ARX_MODE_GRAPH) {
+    rc = calibrate(E, P->n);
+    if (rc) return rc;
+  }
+  for (Level &L : P->levels) {
+    L.shape = mode == ARX_MODE_GRAPH ? tuned_shape(E, L.br_cnt, P->n) : heuristic_shape(E, L.br_cnt);
+    L.grid = grid_for(E, L.shape, std::max(1, L.br_cnt));
+  }
+  const size_t wires = (size_t)nl->num_inputs + nl->num_gates;
+  CK(P->wires.reserve(std::max<size_t>(wires, 1) * kWireStride * 4));
+  CK(P->brjobs.reserve(std::max<size_t>(br.size(), 1) * sizeof(BrJob)));
+  CK(P->ksjobs.reserve(std::max<size_t>(ksj.size(), 1) * sizeof(KsJob)));
+  CK(P->brout.reserve((size_t)std::max(max_br, 1) * kOutStride * 4));
+  CK(P->outidx.reserve(std::max<size_t>(P->outputs.size(), 1) * 4));
+  if (!br.empty()) CK(cudaMemcpy(P->brjobs.p, br.data(), br.size() * sizeof(BrJob), cudaMemcpyHostToDevice));
+  if (!ksj.empty()) CK(cudaMemcpy(P->ksjobs.p, ksj.data(), ksj.size() * sizeof(KsJob), cudaMemcpyHostToDevice));
+  if (!P->outputs.empty())
+    CK(cudaMemcpy(P->outidx.p, P->outputs.data(), P->outputs.size() * 4, cudaMemcpyHostToDevice));
+  out = std::move(P);
+  return ARX_OK;
+}
+
+int plan_launch_levels(Engine &E, Plan &P, cudaStream_t st) {
+  Keyset &ks = E.keysets[P.keyset];
+  for (const Level &L : P.levels) {
+    if (L.br_cnt) {
+      BrArgs a{};
+      a.bsk = ks.bsk;
+      a.wires = P.wires.as<uint32_t>();
+      a.jobs = P.brjobs.as<BrJob>() + L.br_off;
+      a.num_jobs = L.br_cnt;
+      a.n = P.n;
+      a.out = P.brout.as<uint32_t>();
+      a.tg = E.tg;
+      a.status = E.status;
+      a.tc = E.tc;
+      CK(launch_br(a, L.shape, L.grid, st));
+    }
+    KsArgs k{};
+    k.ksk = ks.ksk;
+    k.br_out = P.brout.as<uint32_t>();
+    k.wires = P.wires.as<uint32_t>();
+    k.jobs = P.ksjobs.as<KsJob>() + L.ks_off;
+    k.n = P.n;
+    k.out = P.wires.as<uint32_t>();
+    k.out_stride = kWireStride;
+    CK(launch_ks(k, L.ks_cnt, st));
+  }
+  return ARX_OK;
+}
+
+int plan_exec(Engine &E, Plan &P, const uint32_t *ct_in, uint32_t *ct_out, cudaStream_t user_st) {
+  cudaStream_t st = user_st ? user_st : E.stream;
+  Keyset *ks = nullptr;
+  int rc = resolve_keyset(E, P.keyset, &ks);
+  if (rc) return rc;
+  const size_t row = (size_t)P.n + 1;
+  if (P.num_inputs) {
+    if (!ct_in) return fail(ARX_EINVAL, "ct_in is null");
+    CK(cudaMemcpy2DAsync(P.wires.p, kWireStride * 4, ct_in, row * 4, row * 4, P.num_inputs, cudaMemcpyDefault, st));
+  }
+  if (P.mode == ARX_MODE_GRAPH) {
+    if (!P.exec) {
+      cudaStream_t cs;
+      CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+      cudaGraph_t g;
+      CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+      int lrc = plan_launch_levels(E, P, cs);
+      cudaError_t ce = cudaStreamEndCapture(cs, &g);
+      cudaStreamDestroy(cs);
+      if (lrc) return lrc;
+      CK(ce);
+      ce = cudaGraphInstantiate(&P.exec, g, 0);
+      cudaGraphDestroy(g);
+      CK(ce);
+    }
+    CK(cudaGraphLaunch(P.exec, st));
+  } else {
+    rc = plan_launch_levels(E, P, st);
+    if (rc) return rc;
+  }
+  const int nout = (int)P.outputs.size();
+  if (nout) {
+    if (!ct_out) return fail(ARX_EINVAL, "ct_out is null");
+    if (is_device_ptr(ct_out)) {
+      CK(launch_gather(P.wires.as<uint32_t>(), P.outidx.as<uint32_t>(), nout, P.n, ct_out, (int)row, st));
+    } else {
+      CK(P.outstage.reserve((size_t)nout * row * 4));
+      CK(launch_gather(P.wires.as<uint32_t>(), P.outidx.as<uint32_t>(), nout, P.n, P.outstage.as<uint32_t>(),
+                       (int)row, st));
+      CK(cudaMemcpyAsync(ct_out, P.outstage.p, (size_t)nout * row * 4, cudaMemcpyDeviceToHost, st));
+    }
+  }
+  if (!user_st) return read_status(E, st);
+  return ARX_OK;
+}
+
+void plan_free(Plan &P) {
+  if (P.exec) cudaGraphExecDestroy(P.exec);
+  P.exec = nullptr;
+  P.wires.release();
+  P.brjobs.release();
+  P.ksjobs.release();
+  P.brout.release();
+  P.outidx.release();
+  P.outstage.release();
+}
+
+// --------------------------------------------------------------------------
+// independent gates
+// --------------------------------------------------------------------------
+int bootstrap_gates(Engine &E, const uint8_t *types, const uint32_t *a, const uint32_t *b, const uint32_t *c,
+                    uint32_t *out, size_t count, int keyset, cudaStream_t user_st) {
+  if (count == 0) return ARX_OK;
+  if (!types || !a || !out) return fail(ARX_EINVAL, "null argument");
+  if (count > (1u << 24)) return fail(ARX_EINVAL, "count %zu too large", count);
+  Keyset *ks = nullptr;
+  int rc = resolve_keyset(E, keyset, &ks);
+  if (rc) return rc;
+  bool need_b = false, need_c = false;
+  for (size_t g = 0; g < count; ++g) {
+    if (types[g] > ARX_CONST1) return fail(ARX_EINVAL, "gate %zu: bad type %u", g, types[g]);
+    need_b |= gate_arity(types[g]) >= 2;
+    need_c |= types[g] == ARX_MUX;
+  }
+  if (need_b && !b) return fail(ARX_EINVAL, "ct_b is null but a gate needs it");
+  if (need_c && !c) return fail(ARX_EINVAL, "ct_c is null but a MUX needs it");
+  cudaStream_t st = user_st ? user_st : E.stream;
+  Workspace &W = E.ws[st];
+  const size_t row = (size_t)ks->n + 1;
+  const uint32_t cnt = (uint32_t)count;
+  std::vector<BrJob> br;
+  std::vector<KsJob> ksj;
+  br.reserve(count);
+  ksj.reserve(count);
+  for (uint32_t g = 0; g < cnt; ++g) emit_gate(types[g], g, cnt + g, 2 * cnt + g, g, br, ksj, 0);
+  const int nin = need_c ? 3 : (need_b ? 2 : 1);
+  CK(W.wires.reserve((size_t)nin * count * kWireStride * 4));
+  CK(W.brjobs.reserve(std::max<size_t>(br.size(), 1) * sizeof(BrJob)));
+  CK(W.ksjobs.reserve(ksj.size() * sizeof(KsJob)));
+  CK(W.brout.reserve(std::max<size_t>(br.size(), 1) * kOutStride * 4));
+  const uint32_t *srcs[3] = {a, b, c};
+  for (int s = 0; s < nin; ++s)
+    CK(cudaMemcpy2DAsync(W.wires.as<uint32_t>() + (size_t)s * count * kWireStride, kWireStride * 4, srcs[s],
+                         row * 4, row * 4, count, cudaMemcpyDefault, st));
+  if (!br.empty()) CK(cudaMemcpyAsync(W.brjobs.p, br.data(), br.size() * sizeof(BrJob), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(W.ksjobs.p, ksj.data(), ksj.size() * sizeof(KsJob), cudaMemcpyHostToDevice, st));
+  if (!br.empty()) {
+    BrArgs args{};
+    args.bsk = ks->bsk;
+    args.wires = W.wires.as<uint32_t>();
+    args.jobs = W.brjobs.as<BrJob>();
+    args.num_jobs = (int)br.size();
+    args.n = ks->n;
+    args.out = W.brout.as<uint32_t>();
+    args.tg = E.tg;
+    args.status = E.status;
+    args.tc = E.tc;
+    const BrShape s = E.tuned_n == ks->n ? tuned_shape(E, args.num_jobs, ks->n) : heuristic_shape(E, args.num_jobs);
+    CK(launch_br(args, s, grid_for(E, s, args.num_jobs), st));
+  }
+  const bool dev_out = is_device_ptr(out);
+  if (!dev_out) CK(W.out.reserve(count * row * 4));
+  KsArgs k{};
+  k.ksk = ks->ksk;
+  k.br_out = W.brout.as<uint32_t>();
+  k.wires = W.wires.as<uint32_t>();
+  k.jobs = W.ksjobs.as<KsJob>();
+  k.n = ks->n;
+  k.out = dev_out ? out : W.out.as<uint32_t>();
+  k.out_stride = (int)row;
+  CK(launch_ks(k, (int)count, st));
+  if (!dev_out) CK(cudaMemcpyAsync(out, W.out.p, count * row * 4, cudaMemcpyDeviceToHost, st));
+  if (!user_st) return read_status(E, st);
+  return ARX_OK;
+}
+
+// --------------------------------------------------------------------------
+// keys
+// --------------------------------------------------------------------------
+size_t keyset_bytes(int n) {
+  return (size_t)n * 6 * kChunkBytes + (size_t)kN * 8 * 3 * kKsRowStride * 4;
+}
+
+int load_keys(Engine &E, const uint32_t *bsk, const uint32_t *ksk, int n, cudaStream_t user_st) {
+  if (!bsk || !ksk) return fail(ARX_EINVAL, "null key pointer");
+  if (n < 1 || n > kMaxLweN) return fail(ARX_EINVAL, "lwe_n %d outside 1..%d", n, kMaxLweN);
+  if (E.budget && E.resident_bytes() + keyset_bytes(n) > E.budget)
+    return fail(ARX_ENOMEM, "key set would exceed the HBM budget");
+  cudaStream_t st = user_st ? user_st : E.stream;
+  Keyset K;
+  K.n = n;
+  const size_t bsk_ntt = (size_t)n * 6 * kChunkBytes;
+  const size_t ksk_dev = (size_t)kN * 8 * 3 * kKsRowStride * 4;
+  const size_t bsk_coef = (size_t)n * 6 * 2 * kN * 4;
+  cudaError_t e = cudaMalloc(&K.bsk, bsk_ntt);
+  if (e == cudaSuccess) e = cudaMalloc(&K.ksk, ksk_dev);
+  uint32_t *tmp = nullptr;
+  const uint32_t *src = bsk;
+  if (e == cudaSuccess && !is_device_ptr(bsk)) {
+    e = cudaMalloc(&tmp, bsk_coef);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(tmp, bsk, bsk_coef, cudaMemcpyHostToDevice, st);
+    src = tmp;
+  }
+  if (e == cudaSuccess) e = launch_bsk_to_ntt(src, n, K.bsk, E.tc, E.tg, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(K.ksk, 0, ksk_dev, st);
+  const size_t row = (size_t)n + 1;
+  for (int v = 1; v < 4 && e == cudaSuccess; ++v)
+    e = cudaMemcpy2DAsync(K.ksk + (size_t)(v - 1) * kKsRowStride, 3 * kKsRowStride * 4, ksk + (size_t)v * row,
+                          4 * row * 4, row * 4, (size_t)kN * 8, cudaMemcpyDefault, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (tmp) cudaFree(tmp);
+  if (e != cudaSuccess) {
+    if (K.bsk) cudaFree(K.bsk);
+    if (K.ksk) cudaFree(K.ksk);
+    return fail(e == cudaErrorMemoryAllocation ? ARX_ENOMEM : ARX_ECUDA, "loading keys: %s", cudaGetErrorString(e));
+  }
+  K.used = true;
+  int slot = -1;
+  for (int i = 0; i < (int)E.keysets.size(); ++i)
+    if (!E.keysets[i].used) {
+      slot = i;
+      break;
+    }
+  if (slot < 0) {
+    slot = (int)E.keysets.size();
+    E.keysets.push_back(K);
+  } else {
+    E.keysets[slot] = K;
+  }
+  E.last = slot;
+  return slot;
+}
+
+int unload_keys(Engine &E, int id) {
+  if (id < 0 || id >= (int)E.keysets.size() || !E.keysets[id].used) return fail(ARX_ENOKEYS, "no key set %d", id);
+  Keyset &K = E.keysets[id];
+  if (K.refs) return fail(ARX_EBUSY, "key set %d is referenced by %d plan(s)", id, K.refs);
+  cudaDeviceSynchronize();
+  cudaFree(K.bsk);
+  cudaFree(K.ksk);
+  K = Keyset{};
+  if (E.last == id) {
+    E.last = -1;
+    for (int i = (int)E.keysets.size() - 1; i >= 0; --i)
+      if (E.keysets[i].used) {
+        E.last = i;
+        break;
+      }
+  }
+  return ARX_OK;
+}
+
+size_t Engine::resident_bytes() const {
+  size_t s = 0;
+  for (const Keyset &k : keysets)
+    if (k.used) s += keyset_bytes(k.n);
+  return s;
+}
+
+}  // namespace arx
+
+// ============================================================================
+// C-ABI
+// ============================================================================
+using namespace arx;
+
+#define API_BEGIN                       \
+  Engine &E = eng();                    \
+  std::lock_guard<std::mutex> lk(E.mu); \
+  {                                     \
+    int rc_ = ensure_init(E);           \
+    if (rc_) return rc_;                \
+  }
+
+extern "C" int arx_load_keys(const uint32_t *bsk, const uint32_t *ksk) {
+  API_BEGIN
+  return load_keys(E, bsk, ksk, ARX_LWE_N, nullptr);
+}
+
+extern "C" int arx_load_keys_ex(const uint32_t *bsk, const uint32_t *ksk, int lwe_n, void *stream) {
+  API_BEGIN
+  return load_keys(E, bsk, ksk, lwe_n, (cudaStream_t)stream);
+}
+
+extern "C" int arx_unload_keys(int keyset) {
+  API_BEGIN
+  return unload_keys(E, keyset);
+}
+
+extern "C" int arx_use_keys(int keyset) {
+  API_BEGIN
+  Keyset *ks = nullptr;
+  if (keyset < 0) return fail(ARX_ENOKEYS, "no key set %d", keyset);
+  int rc = resolve_keyset(E, keyset, &ks);
+  if (rc) return rc;
+  E.last = keyset;
+  return ARX_OK;
+}
+
+extern "C" size_t arx_keyset_bytes(int lwe_n) { return lwe_n < 1 || lwe_n > kMaxLweN ? 0 : keyset_bytes(lwe_n); }
+
+extern "C" int arx_bootstrap_gates(const uint8_t *types, const uint32_t *ct_a, const uint32_t *ct_b,
+                                   uint32_t *ct_out, size_t count) {
+  API_BEGIN
+  for (size_t g = 0; g < count && types; ++g)
+    if (types[g] == ARX_MUX) return fail(ARX_EINVAL, "MUX needs arx_bootstrap_gates_ex (third input)");
+  return bootstrap_gates(E, types, ct_a, ct_b, nullptr, ct_out, count, -1, nullptr);
+}
+
+extern "C" int arx_bootstrap_gates_ex(const uint8_t *types, const uint32_t *ct_a, const uint32_t *ct_b,
+                                      const uint32_t *ct_c, uint32_t *ct_out, size_t count, int keyset,
+                                      void *stream) {
+  API_BEGIN
+  return bootstrap_gates(E, types, ct_a, ct_b, ct_c, ct_out, count, keyset, (cudaStream_t)stream);
+}
+
+extern "C" int arx_levelize(const arx_netlist *nl, uint32_t *wave, uint32_t *depth) {
+  if (!wave && nl && nl->num_gates) return fail(ARX_EINVAL, "wave is null");
+  uint32_t dummy = 0;
+  return levelize(nl, wave ? wave : &dummy, depth);
+}
+
+extern "C" int arx_eval_netlist_ex(const arx_netlist *nl, const uint32_t *ct_in, uint32_t *ct_out, int keyset,
+                                   int mode, void *stream) {
+  API_BEGIN
+  if (mode != ARX_MODE_PLAIN && mode != ARX_MODE_GRAPH) return fail(ARX_EINVAL, "bad mode %d", mode);
+  std::unique_ptr<Plan> P;
+  int rc = plan_build(E, nl, keyset, mode, P);
+  if (rc) return rc;
+  rc = plan_exec(E, *P, ct_in, ct_out, (cudaStream_t)stream);
+  if (stream) cudaStreamSynchronize((cudaStream_t)stream);  // the plan's buffers are freed below
+  plan_free(*P);
+  return rc;
+}
+
+extern "C" int arx_eval_netlist(const arx_netlist *nl, const uint32_t *ct_in, uint32_t *ct_out) {
+  return arx_eval_netlist_ex(nl, ct_in, ct_out, -1, ARX_MODE_PLAIN, nullptr);
+}
+
+extern "C" int arx_plan_create(const arx_netlist *nl, int keyset, int mode) {
+  API_BEGIN
+  if (mode != ARX_MODE_PLAIN && mode != ARX_MODE_GRAPH) return fail(ARX_EINVAL, "bad mode %d", mode);
+  std::unique_ptr<Plan> P;
+  int rc = plan_build(E, nl, keyset, mode, P);
+  if (rc) return rc;
+  E.keysets[P->keyset].refs++;
+  for (int i = 0; i < (int)E.plans.size(); ++i)
+    if (!E.plans[i]) {
+      E.plans[i] = std::move(P);
+      return i;
+    }
+  E.plans.push_back(std::move(P));
+  return (int)E.plans.size() - 1;
+}
+
+extern "C" int arx_plan_run(int plan, const uint32_t *ct_in, uint32_t *ct_out, void *stream) {
+  API_BEGIN
+  if (plan < 0 || plan >= (int)E.plans.size() || !E.plans[plan]) return fail(ARX_EINVAL, "no plan %d", plan);
+  return plan_exec(E, *E.plans[plan], ct_in, ct_out, (cudaStream_t)stream);
+}
+
+extern "C" int arx_plan_destroy(int plan) {
+  API_BEGIN
+  if (plan < 0 || plan >= (int)E.plans.size() || !E.plans[plan]) return fail(ARX_EINVAL, "no plan %d", plan);
+  cudaDeviceSynchronize();
+  E.keysets[E.plans[plan]->keyset].refs--;
+  plan_free(*E.plans[plan]);
+  E.plans[plan].reset();
+  return ARX_OK;
+}
+
+extern "C" int arx_plan_info(int plan, uint32_t *waves, uint64_t *bootstraps, uint64_t *gates) {
+  API_BEGIN
+  if (plan < 0 || plan >= (int)E.plans.size() || !E.plans[plan]) return fail(ARX_EINVAL, "no plan %d", plan);
+  const Plan &P = *E.plans[plan];
+  if (waves) *waves = (uint32_t)P.levels.size();
+  if (bootstraps) *bootstraps = P.bootstraps;
+  if (gates) *gates = P.num_gates;
+  return ARX_OK;
+}
+
+extern "C" int arx_plan_wires(int plan, const uint32_t *ids, size_t count, uint32_t *out) {
+  API_BEGIN
+  if (plan < 0 || plan >= (int)E.plans.size() || !E.plans[plan]) return fail(ARX_EINVAL, "no plan %d", plan);
+  Plan &P = *E.plans[plan];
+  if (!count) return ARX_OK;
+  if (!ids || !out) return fail(ARX_EINVAL, "null argument");
+  const uint64_t wires = (uint64_t)P.num_inputs + P.num_gates;
+  for (size_t k = 0; k < count; ++k)
+    if (ids[k] >= wires) return fail(ARX_EINVAL, "wire %u out of range", ids[k]);
+  const size_t row = (size_t)P.n + 1;
+  DevBuf idx, stage;
+  CK(idx.reserve(count * 4));
+  CK(cudaMemcpyAsync(idx.p, ids, count * 4, cudaMemcpyHostToDevice, E.stream));
+  const bool dev = is_device_ptr(out);
+  if (!dev) CK(stage.reserve(count * row * 4));
+  CK(launch_gather(P.wires.as<uint32_t>(), idx.as<uint32_t>(), (int)count, P.n, dev ? out : stage.as<uint32_t>(),
+                   (int)row, E.stream));
+  if (!dev) CK(cudaMemcpyAsync(out, stage.p, count * row * 4, cudaMemcpyDeviceToHost, E.stream));
+  CK(cudaStreamSynchronize(E.stream));
+  idx.release();
+  stage.release();
+  return ARX_OK;
+}
+
+extern "C" int arx_plan_profile(int plan, const uint32_t *ct_in, float *br_ms, float *ks_ms,
+                                uint32_t *br_launches, uint32_t *ks_launches) {
+  API_BEGIN
+  if (plan < 0 || plan >= (int)E.plans.size() || !E.plans[plan]) return fail(ARX_EINVAL, "no plan %d", plan);
+  Plan &P = *E.plans[plan];
+  Keyset *ks = nullptr;
+  int rc = resolve_keyset(E, P.keyset, &ks);
+  if (rc) return rc;
+  cudaStream_t st = E.stream;
+  const size_t row = (size_t)P.n + 1;
+  if (P.num_inputs) {
+    if (!ct_in) return fail(ARX_EINVAL, "ct_in is null");
+    CK(cudaMemcpy2DAsync(P.wires.p, kWireStride * 4, ct_in, row * 4, row * 4, P.num_inputs, cudaMemcpyDefault, st));
+  }
+  std::vector<cudaEvent_t> ev(4 * P.levels.size() + 1);
+  for (auto &e : ev) CK(cudaEventCreate(&e));
+  uint32_t nb = 0, nk = 0;
+  for (size_t l = 0; l < P.levels.size(); ++l) {
+    const Level &L = P.levels[l];
+    CK(cudaEventRecord(ev[4 * l], st));
+    if (L.br_cnt) {
+      BrArgs a{};
+      a.bsk = ks->bsk;
+      a.wires = P.wires.as<uint32_t>();
+      a.jobs = P.brjobs.as<BrJob>() + L.br_off;
+      a.num_jobs = L.br_cnt;
+      a.n = P.n;
+      a.out = P.brout.as<uint32_t>();
+      a.tg = E.tg;
+      a.status = E.status;
+      a.tc = E.tc;
+      CK(launch_br(a, L.shape, L.grid, st));
+      ++nb;
+    }
+    CK(cudaEventRecord(ev[4 * l + 1], st));
+    CK(cudaEventRecord(ev[4 * l + 2], st));
+    KsArgs k{};
+    k.ksk = ks->ksk;
+    k.br_out = P.brout.as<uint32_t>();
+    k.wires = P.wires.as<uint32_t>();
+    k.jobs = P.ksjobs.as<KsJob>() + L.ks_off;
+    k.n = P.n;
+    k.out = P.wires.as<uint32_t>();
+    k.out_stride = kWireStride;
+    CK(launch_ks(k, L.ks_cnt, st));
+    if (L.ks_cnt) ++nk;
+    CK(cudaEventRecord(ev[4 * l + 3], st));
+  }
+  CK(cudaStreamSynchronize(st));
+  float tb = 0, tk = 0;
+  for (size_t l = 0; l < P.levels.size(); ++l) {
+    float x = 0, y = 0;
+    CK(cudaEventElapsedTime(&x, ev[4 * l], ev[4 * l + 1]));
+    CK(cudaEventElapsedTime(&y, ev[4 * l + 2], ev[4 * l + 3]));
+    tb += x;
+    tk += y;
+  }
+  for (auto &e : ev) cudaEventDestroy(e);
+  if (br_ms) *br_ms = tb;
+  if (ks_ms) *ks_ms = tk;
+  if (br_launches) *br_launches = nb;
+  if (ks_launches) *ks_launches = nk;
+  return read_status(E, st);
+}
+
+extern "C" int arx_set_launch_shape(int H, int GT) {
+  Engine &E = eng();
+  std::lock_guard<std::mutex> lk(E.mu);
+  if (H == 0 && GT == 0) {
+    E.forced = BrShape{0, 0};
+    return ARX_OK;
+  }
+  if (!br_shape_supported(BrShape{H, GT})) return fail(ARX_EINVAL, "unsupported launch shape (%d, %d)", H, GT);
+  E.forced = BrShape{H, GT};
+  return ARX_OK;
+}
+
+extern "C" const char *arx_last_error(void) { return t_err.c_str(); }
+
+extern "C" int arx_device_status(void) {
+  API_BEGIN
+  return read_status(E, E.stream);
+}
+
+extern "C" int arx_device_sms(void) { return eng().sms; }

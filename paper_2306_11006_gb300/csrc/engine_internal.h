@@ -1,0 +1,100 @@
+// engine_internal.h -- host-side state of libarx shared by engine.cpp and serve.cpp.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/arx.h"
+#include "arx_kernels.h"
+
+namespace arx {
+
+struct DevBuf {
+  void *p = nullptr;
+  size_t cap = 0;
+  cudaError_t reserve(size_t bytes);
+  void release();
+  template <class T>
+  T *as() const { return reinterpret_cast<T *>(p); }
+};
+
+struct Keyset {
+  bool used = false;
+  int n = 0;
+  uint32_t *bsk = nullptr;  // NTT-domain bootstrapping key
+  uint32_t *ksk = nullptr;  // [N][8][3][632]
+  int refs = 0;             // plans referencing it
+};
+
+struct Workspace {
+  DevBuf wires, brjobs, ksjobs, brout, out;
+};
+
+struct Level {
+  int br_off = 0, br_cnt = 0, ks_off = 0, ks_cnt = 0;
+  BrShape shape{1, 1};
+  int grid = 1;
+};
+
+struct Plan {
+  int keyset = -1, n = 0, mode = 0;
+  uint32_t num_inputs = 0, num_gates = 0;
+  std::vector<uint32_t> outputs;
+  std::vector<Level> levels;
+  uint64_t bootstraps = 0;
+  DevBuf wires, brjobs, ksjobs, brout, outidx, outstage;
+  cudaGraphExec_t exec = nullptr;
+};
+
+struct TuneEntry {
+  BrShape shape{1, 1};
+  double wave_ms_per_cmux = 0;
+  int gates_per_wave = 0;
+};
+
+struct Engine {
+  std::mutex mu;
+  bool ready = false;
+  int device = 0;
+  int sms = 0;
+  size_t smem_optin = 0;
+  TwiddleConst tc{};
+  TwiddleGlobal *tg = nullptr;
+  unsigned int *status = nullptr;
+  cudaStream_t stream = nullptr;
+  std::vector<Keyset> keysets;
+  int last = -1;
+  size_t budget = 0;  // HBM budget for resident keys (0 = none)
+  std::map<cudaStream_t, Workspace> ws;
+  std::vector<std::unique_ptr<Plan>> plans;
+  std::vector<TuneEntry> tune;
+  int tuned_n = -1;
+  std::vector<std::pair<BrShape, int>> occ;  // resident CTAs per SM of each shape
+  BrShape forced{0, 0};  // launch-shape override (H = 0: automatic)
+  size_t resident_bytes() const;
+};
+
+Engine &eng();
+int fail(int code, const char *fmt, ...);
+int ensure_init(Engine &E);
+bool is_device_ptr(const void *p);
+int resolve_keyset(Engine &E, int keyset, Keyset **out);
+int read_status(Engine &E, cudaStream_t st);
+int gate_arity(uint32_t type);
+void emit_gate(uint32_t type, uint32_t w0, uint32_t w1, uint32_t w2, uint32_t out, std::vector<BrJob> &br,
+               std::vector<KsJob> &ks, uint32_t br_base);
+BrShape heuristic_shape(Engine &E, int jobs);
+BrShape tuned_shape(Engine &E, int jobs, int n);
+int grid_for(Engine &E, BrShape s, int jobs);
+int calibrate(Engine &E, int n);
+int levelize(const arx_netlist *nl, uint32_t *wave, uint32_t *depth);
+size_t keyset_bytes(int n);
+
+}  // namespace arx

@@ -1,0 +1,304 @@
+"""GPU parity: every ciphertext the CUDA path produces is bit-identical to the
+CPU oracle's on the same inputs (tolerance 0: the method is exact integer
+arithmetic mod 2^32), and every decrypted output is correct.
+
+Sizes the oracle finishes in seconds are compared in full; the full-size
+workloads (the 32-bit adder and 8x8 multiplier, the 65,536-gate random DAG, the
+eight 4x4 matrix products) are compared on sampled gates, each recomputed by the
+oracle from the GPU's own input wires, plus the decrypted results of all outputs.
+"""
+import numpy as np
+import pytest
+
+from paper_2306_11006_gb300 import arx
+from paper_2306_11006_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(6, 1), (3, 1), (3, 2), (2, 1), (2, 3), (1, 1), (1, 2), (1, 4), (1, 6)]
+
+
+@pytest.fixture(scope="session")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+@pytest.fixture(scope="session")
+def _loaded630(torch_cuda, keys630):
+    return arx.load_keys(keys630.bsk, keys630.ksk, 630)
+
+
+@pytest.fixture(scope="session")
+def _loaded64(torch_cuda, keys64):
+    return arx.load_keys(keys64.bsk, keys64.ksk, 64)
+
+
+@pytest.fixture
+def gpu630(_loaded630):
+    arx.use_keys(_loaded630)   # the default key set of the calls without an id
+    return _loaded630
+
+
+@pytest.fixture
+def gpu64(_loaded64, _loaded630):
+    arx.use_keys(_loaded630)
+    return _loaded64
+
+
+def _inputs(O, I_, keys, types, seed):
+    m = len(types)
+    xs, ys, zs = I_.random_bits(seed, m), I_.random_bits(seed + 1, m), I_.random_bits(seed + 2, m)
+    return (xs, ys, zs, keys.encrypt(O, I_, xs, seed + 3), keys.encrypt(O, I_, ys, seed + 4),
+            keys.encrypt(O, I_, zs, seed + 5))
+
+
+def _truth(types, xs, ys, zs):
+    return np.array([I._plain_gate(int(t), [int(x), int(y), int(z)]) for t, x, y, z in zip(types, xs, ys, zs)],
+                    np.uint8)
+
+
+def test_config1_64_independent_gates(O, keys630, gpu630):
+    types = I.random_gate_types(1, 64)
+    xs, ys, zs, ca, cb, cc = _inputs(O, I, keys630, types, 10)
+    out = np.zeros_like(ca)
+    arx.bootstrap_gates(types, ca, cb, out)
+    want = keys630.ctx.gates(types, ca, cb)
+    assert np.array_equal(out, want)
+    assert np.array_equal(arx.client_decrypt(630, keys630.s, out), _truth(types, xs, ys, zs))
+
+
+def test_all_gate_types_with_mux(O, keys630, gpu630):
+    types = np.array(list(range(11)) * 3, np.uint8)
+    xs, ys, zs, ca, cb, cc = _inputs(O, I, keys630, types, 20)
+    out = np.zeros_like(ca)
+    arx.bootstrap_gates_ex(types, ca, cb, cc, out, keyset=gpu630)
+    want = keys630.ctx.gates(types, ca, cb, cc)
+    assert np.array_equal(out, want)
+    assert np.array_equal(arx.client_decrypt(630, keys630.s, out), _truth(types, xs, ys, zs))
+
+
+def test_every_launch_shape_ragged(O, keys630, gpu630):
+    """37 gates (a ragged tail for every gates-per-CTA tile) under each shape."""
+    types = np.array([I.BINARY_OPS[k % 6] if k % 9 else I.MUX for k in range(37)], np.uint8)
+    xs, ys, zs, ca, cb, cc = _inputs(O, I, keys630, types, 30)
+    want = keys630.ctx.gates(types, ca, cb, cc)
+    try:
+        for H, GT in SHAPES:
+            arx.set_launch_shape(H, GT)
+            out = np.zeros_like(ca)
+            arx.bootstrap_gates_ex(types, ca, cb, cc, out, keyset=gpu630)
+            assert np.array_equal(out, want), (H, GT)
+    finally:
+        arx.set_launch_shape(0, 0)
+
+
+def test_persistent_tiles_beyond_one_wave_sampled(O, keys630, gpu630):
+    """More tiles than resident CTAs: the persistent loop wraps; sampled gates."""
+    count = 2000
+    types = I.random_gate_types(40, count)
+    xs, ys, zs, ca, cb, cc = _inputs(O, I, keys630, types, 41)
+    out = np.zeros_like(ca)
+    try:
+        arx.set_launch_shape(1, 2)
+        arx.bootstrap_gates(types, ca, cb, out)
+    finally:
+        arx.set_launch_shape(0, 0)
+    assert np.array_equal(arx.client_decrypt(630, keys630.s, out), _truth(types, xs, ys, zs))
+    pick = np.unique(np.concatenate([np.arange(3), np.arange(count - 3, count),
+                                     np.random.default_rng(0).choice(count, 26, replace=False)]))
+    want = keys630.ctx.gates(types[pick], ca[pick], cb[pick])
+    assert np.array_equal(out[pick], want)
+
+
+def test_device_pointers_and_streams(O, keys630, gpu630, torch_cuda):
+    torch = torch_cuda
+    types = I.random_gate_types(50, 24)
+    xs, ys, zs, ca, cb, cc = _inputs(O, I, keys630, types, 51)
+    want = keys630.ctx.gates(types, ca, cb)
+    da, db = torch.from_numpy(ca.view(np.int32)).cuda(), torch.from_numpy(cb.view(np.int32)).cuda()
+    dout = torch.zeros_like(da)
+    s = torch.cuda.Stream()
+    arx.bootstrap_gates_ex(types, da, db, None, dout, keyset=gpu630, stream=s)
+    s.synchronize()
+    assert arx.device_status() == 0
+    assert np.array_equal(dout.cpu().numpy().view(np.uint32), want)
+
+
+def test_empty_and_single_gate(O, keys630, gpu630):
+    arx.bootstrap_gates(np.zeros(0, np.uint8), np.zeros((0, 631), np.uint32), np.zeros((0, 631), np.uint32),
+                        np.zeros((0, 631), np.uint32))
+    types = np.array([I.NAND], np.uint8)
+    xs, ys, zs, ca, cb, cc = _inputs(O, I, keys630, types, 60)
+    out = np.zeros_like(ca)
+    arx.bootstrap_gates(types, ca, cb, out)
+    assert np.array_equal(out, keys630.ctx.gates(types, ca, cb))
+
+
+def test_linear_only_gates(O, keys630, gpu630):
+    types = np.array([I.NOT, I.COPY, I.CONST0, I.CONST1] * 5, np.uint8)
+    xs, ys, zs, ca, cb, cc = _inputs(O, I, keys630, types, 70)
+    out = np.zeros_like(ca)
+    arx.bootstrap_gates(types, ca, cb, out)
+    assert np.array_equal(out, keys630.ctx.gates(types, ca, cb))
+
+
+def test_second_keyset_smaller_dimension(O, keys64, gpu64, gpu630):
+    types = np.array(list(range(11)) * 2, np.uint8)
+    xs, ys, zs, ca, cb, cc = _inputs(O, I, keys64, types, 80)
+    out = np.zeros_like(ca)
+    arx.bootstrap_gates_ex(types, ca, cb, cc, out, keyset=gpu64)
+    assert np.array_equal(out, keys64.ctx.gates(types, ca, cb, cc))
+
+
+def test_invalid_arguments_are_rejected(gpu630):
+    with pytest.raises(arx.ArxError) as e:
+        arx.bootstrap_gates(np.array([11], np.uint8), np.zeros((1, 631), np.uint32),
+                            np.zeros((1, 631), np.uint32), np.zeros((1, 631), np.uint32))
+    assert e.value.code == -1
+    with pytest.raises(arx.ArxError) as e:
+        arx.bootstrap_gates_ex(np.array([0], np.uint8), np.zeros((1, 631), np.uint32),
+                               np.zeros((1, 631), np.uint32), None, np.zeros((1, 631), np.uint32), keyset=99)
+    assert e.value.code == -2
+    with pytest.raises(arx.ArxError) as e:
+        arx.bootstrap_gates(np.array([I.MUX], np.uint8), np.zeros((1, 631), np.uint32),
+                            np.zeros((1, 631), np.uint32), np.zeros((1, 631), np.uint32))
+    assert e.value.code == -1
+
+
+# --------------------------------------------------------------------------
+# netlists
+# --------------------------------------------------------------------------
+def _encrypt_inputs(O, keys, nl, seed):
+    bits = I.random_bits(seed, nl.num_inputs)
+    return bits, keys.encrypt(O, I, bits, seed + 1)
+
+
+def test_small_netlists_bit_exact_in_full(O, keys630, gpu630):
+    for nl in (I.ripple_carry_adder(4), I.array_multiplier(3), I.comparator(3)):
+        bits, ct = _encrypt_inputs(O, keys630, nl, 90)
+        out = np.zeros((len(nl.outputs), 631), np.uint32)
+        arx.eval_netlist(nl, ct, out)
+        assert np.array_equal(out, keys630.ctx.eval_netlist(nl, ct)), nl.name
+        assert np.array_equal(arx.client_decrypt(630, keys630.s, out), nl.plain_eval(bits))
+
+
+def test_graph_mode_equals_plain_mode(O, keys630, gpu630):
+    nl = I.union([I.ripple_carry_adder(5), I.comparator(4)])
+    bits, ct = _encrypt_inputs(O, keys630, nl, 95)
+    a = np.zeros((len(nl.outputs), 631), np.uint32)
+    b = np.zeros_like(a)
+    arx.eval_netlist_ex(nl, ct, a, mode=arx.MODE_PLAIN)
+    with arx.Plan(nl, mode=arx.MODE_GRAPH) as p:
+        p.run(ct, b)
+        c = np.zeros_like(a)
+        p.run(ct, c)  # replay of the captured graph
+    assert np.array_equal(a, b) and np.array_equal(a, c)
+    assert np.array_equal(arx.client_decrypt(630, keys630.s, a), nl.plain_eval(bits))
+
+
+def _sampled_gate_parity(O, keys, nl, plan, per_level=8, levels=3, seed=0):
+    wave, depth = arx.levelize(nl)
+    rng = np.random.default_rng(seed)
+    lv = sorted(set([0, depth // 2, depth - 1] + list(rng.integers(0, depth, max(0, levels - 3)))))
+    gates = []
+    for L in lv:
+        idx = np.nonzero(wave == L)[0]
+        gates += list(rng.choice(idx, min(per_level, len(idx)), replace=False))
+    gates = np.array(sorted(gates))
+    ins = np.stack([nl.in0[gates], nl.in1[gates], nl.in2[gates]])
+    w_in = plan.wires(ins.ravel(), keys.n).reshape(3, len(gates), keys.n + 1)
+    w_out = plan.wires(nl.num_inputs + gates, keys.n)
+    # inputs a gate does not read are ignored by both sides
+    want = keys.ctx.gates(nl.type[gates], w_in[0], w_in[1], w_in[2])
+    assert np.array_equal(w_out, want), [int(g) for g in gates[np.any(w_out != want, axis=1)]]
+    return len(gates)
+
+
+@pytest.mark.parametrize("mode", [arx.MODE_PLAIN, arx.MODE_GRAPH])
+def test_config2_adder32_and_mult8(O, keys630, gpu630, mode):
+    adder, mult = I.ripple_carry_adder(32), I.array_multiplier(8)
+    nl = I.union([adder, mult])
+    rng = np.random.default_rng(2)
+    a, b, cin = (int(x) for x in rng.integers(0, 2 ** 32, 2)) + (int(rng.integers(0, 2)),)
+    x, y = (int(v) for v in rng.integers(0, 256, 2))
+    bits = I.int_to_bits(a, 32) + I.int_to_bits(b, 32) + [cin] + I.int_to_bits(x, 8) + I.int_to_bits(y, 8)
+    ct = keys630.encrypt(O, I, bits, 200)
+    out = np.zeros((len(nl.outputs), 631), np.uint32)
+    with arx.Plan(nl, mode=mode) as p:
+        p.run(ct, out)
+        dec = arx.client_decrypt(630, keys630.s, out)
+        assert I.bits_to_int(dec[:33]) == a + b + cin
+        assert I.bits_to_int(dec[33:]) == x * y
+        assert _sampled_gate_parity(O, keys630, nl, p, per_level=6, levels=5) >= 20
+
+
+def test_config3_random_dag_sampled(O, keys630, gpu630):
+    nl = I.random_dag(seed=3)
+    bits, ct = _encrypt_inputs(O, keys630, nl, 300)
+    out = np.zeros((len(nl.outputs), 631), np.uint32)
+    with arx.Plan(nl, mode=arx.MODE_GRAPH) as p:
+        assert p.waves == 40 and p.gates == 65536
+        p.run(ct, out)
+        assert arx.device_status() == 0
+        assert np.array_equal(arx.client_decrypt(630, keys630.s, out), nl.plain_eval(bits))
+        assert _sampled_gate_parity(O, keys630, nl, p, per_level=6, levels=6, seed=3) >= 30
+
+
+def test_config4_matmul_instances_sampled(O, keys630, gpu630):
+    inst = [I.matmul4x4() for _ in range(8)]
+    nl = I.union(inst)
+    rng = np.random.default_rng(4)
+    A = rng.integers(0, 256, (8, 4, 4))
+    B = rng.integers(0, 256, (8, 4, 4))
+    bits = []
+    for k in range(8):
+        for v in list(A[k].ravel()) + list(B[k].ravel()):
+            bits += I.int_to_bits(int(v), 8)
+    ct = keys630.encrypt(O, I, bits, 400)
+    out = np.zeros((len(nl.outputs), 631), np.uint32)
+    with arx.Plan(nl, mode=arx.MODE_GRAPH) as p:
+        p.run(ct, out)
+        dec = arx.client_decrypt(630, keys630.s, out).reshape(8, 16, 16)
+        for k in range(8):
+            C = (A[k] @ B[k]) % (1 << 16)
+            got = np.array([I.bits_to_int(dec[k, e]) for e in range(16)]).reshape(4, 4)
+            assert np.array_equal(got, C), k
+        assert _sampled_gate_parity(O, keys630, nl, p, per_level=4, levels=6, seed=4) >= 20
+
+
+def test_netlist_edge_cases(O, keys630, gpu630):
+    # no gates: outputs are inputs
+    nl0 = I.Netlist(3, np.zeros(0, np.uint8), *(np.zeros(0, np.uint32),) * 3, np.array([2, 0], np.uint32))
+    bits, ct = _encrypt_inputs(O, keys630, nl0, 500)
+    out = np.zeros((2, 631), np.uint32)
+    arx.eval_netlist(nl0, ct, out)
+    assert np.array_equal(out, ct[[2, 0]])
+    # linear-only chain and constants, MUX-heavy netlist
+    B = I.Builder(3)
+    w = B.NOT(0)
+    w = B.NOT(w)
+    c1 = B.gate(I.CONST1)
+    m = B.MUX(0, 1, 2)
+    m2 = B.MUX(m, c1, B.NOT(1))
+    cp = B.gate(I.COPY, m2)
+    nl = B.build([w, c1, m, m2, cp])
+    for trial in range(2):
+        bits, ct = _encrypt_inputs(O, keys630, nl, 510 + trial)
+        out = np.zeros((len(nl.outputs), 631), np.uint32)
+        arx.eval_netlist(nl, ct, out)
+        assert np.array_equal(out, keys630.ctx.eval_netlist(nl, ct))
+        assert np.array_equal(arx.client_decrypt(630, keys630.s, out), nl.plain_eval(bits))
+
+
+def test_plan_keeps_keyset_busy(gpu630, keys64, torch_cuda):
+    ks = arx.load_keys(keys64.bsk, keys64.ksk, 64)
+    p = arx.Plan(I.comparator(2), keyset=ks, mode=arx.MODE_PLAIN)
+    with pytest.raises(arx.ArxError) as e:
+        arx.unload_keys(ks)
+    assert e.value.code == -7
+    p.close()
+    arx.unload_keys(ks)
+    arx.use_keys(gpu630)
