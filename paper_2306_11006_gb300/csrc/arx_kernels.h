@@ -74,6 +74,9 @@ struct KsArgs {
   int n;
   uint32_t *out;           // destination rows (out_stride words apart)
   int out_stride;
+  int splits;              // CTAs per gate: each sums N / splits of the key rows
+  uint32_t *partial;       // scratch [jobs][splits][632] (splits > 1)
+  unsigned int *counters;  // scratch [jobs], zero between launches (splits > 1)
 };
 
 struct BrShape {
@@ -92,6 +95,8 @@ bool br_shape_supported(BrShape s);
 int br_occupancy(BrShape s);  // resident CTAs per SM (0: cannot launch)
 cudaError_t launch_br(const BrArgs &args, BrShape s, int grid, cudaStream_t st);
 cudaError_t launch_ks(const KsArgs &args, int num_jobs, cudaStream_t st);
+// Splits of the key-switch gather for a wave of num_jobs gates on sms SMs.
+int ks_splits(int num_jobs, int sms);
 cudaError_t launch_gather(const uint32_t *wires, const uint32_t *idx, int count, int n, uint32_t *dst,
                           int dst_stride, cudaStream_t st);
 

@@ -145,20 +145,32 @@ struct BrShared {
   volatile int *abort_flag;
 };
 
-constexpr int kStages = 4;
 constexpr int kAbarPitch = 640;
+constexpr size_t kSmemLimit = 227 * 1024;  // opt-in shared memory per CTA
 
 template <int H>
 __host__ __device__ constexpr int scratch_words() { return (H == 1 ? 1 : 2) * kXpose; }
 
 template <int H, int GT>
+constexpr size_t br_fixed_bytes() {
+  return (size_t)GT * 4 * kN * 4 + (size_t)2 * H * GT * scratch_words<H>() * 4 + (size_t)GT * kAbarPitch * 2 + 2 * 8 * 8 + 16;
+}
+
+// Ring depth: as many key rows in flight as shared memory allows, 4..8.
+template <int H, int GT>
+__host__ __device__ constexpr int br_stages() {
+  return (kSmemLimit - br_fixed_bytes<H, GT>()) / kChunkBytes >= 8 ? 8
+         : (int)((kSmemLimit - br_fixed_bytes<H, GT>()) / kChunkBytes);
+}
+
+template <int H, int GT>
 constexpr size_t br_smem_bytes() {
-  return (size_t)kStages * kChunkBytes + (size_t)GT * 4 * kN * 4 +
-         (size_t)2 * H * GT * scratch_words<H>() * 4 + (size_t)GT * kAbarPitch * 2 + 2 * kStages * 8 + 16;
+  return (size_t)br_stages<H, GT>() * kChunkBytes + br_fixed_bytes<H, GT>();
 }
 
 template <int H, int GT>
 __device__ __forceinline__ BrShared br_carve(uint8_t *smem) {
+  constexpr int kStages = br_stages<H, GT>();
   BrShared s;
   s.ring = reinterpret_cast<uint32_t *>(smem);
   s.acc = s.ring + kStages * kChunkWords;
@@ -188,6 +200,7 @@ __device__ __forceinline__ void br_consumer(const BrShared &S, const BrArgs &arg
   uint32_t *myscr = S.scratch + (wbase + role) * kScr;
   const uint2 *tw2 = args.tg->fwd2[P];
   const uint2 *tw1 = args.tg->inv1[P];
+  constexpr int kStages = br_stages<H, GT>();
   const int tiles = (args.num_jobs + GT - 1) / GT;
   uint32_t it = 0;
 
@@ -349,6 +362,8 @@ __global__ void __launch_bounds__((2 * H * GT + 1) * 32, 1) br_kernel(const __gr
   BrShared S = br_carve<H, GT>(smem);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int kCons = 2 * H * GT;
+  constexpr int kStages = br_stages<H, GT>();
+  static_assert(kStages >= 4 && kStages <= 8, "ring depth");
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(S.full + s, 1);

@@ -337,6 +337,18 @@ int levelize(const arx_netlist *nl, uint32_t *wave, uint32_t *depth) {
   return ARX_OK;
 }
 
+// Key-switch scratch: partial sums [jobs][splits][632] and zeroed counters [jobs].
+int reserve_ks_scratch(DevBuf &part, DevBuf &cnt, size_t jobs, int splits) {
+  if (splits <= 1 || !jobs) return ARX_OK;
+  const size_t pbytes = jobs * (size_t)splits * kKsRowStride * 4;
+  if (pbytes > part.cap) CK(part.reserve(pbytes));
+  if (jobs * 4 > cnt.cap) {
+    CK(cnt.reserve(jobs * 4));
+    CK(cudaMemset(cnt.p, 0, cnt.cap));
+  }
+  return ARX_OK;
+}
+
 // --------------------------------------------------------------------------
 // plans
 // --------------------------------------------------------------------------
@@ -385,9 +397,20 @@ int plan_build(Engine &E, const arx_netlist *nl, int keyset, int mode, std::uniq
     rc = calibrate(E, P->n);
     if (rc) return rc;
   }
+  size_t ks_part_max = 0, ks_gate_max = 0;
   for (Level &L : P->levels) {
     L.shape = mode == ARX_MODE_GRAPH ? tuned_shape(E, L.br_cnt, P->n) : heuristic_shape(E, L.br_cnt);
     L.grid = grid_for(E, L.shape, std::max(1, L.br_cnt));
+    L.ks_splits = ks_splits(L.ks_cnt, E.sms);
+    if (L.ks_splits > 1) {
+      ks_part_max = std::max(ks_part_max, (size_t)L.ks_cnt * L.ks_splits);
+      ks_gate_max = std::max(ks_gate_max, (size_t)L.ks_cnt);
+    }
+  }
+  if (ks_part_max) {
+    CK(P->kspart.reserve(ks_part_max * kKsRowStride * 4));
+    CK(P->kscnt.reserve(ks_gate_max * 4));
+    CK(cudaMemset(P->kscnt.p, 0, P->kscnt.cap));
   }
   const size_t wires = (size_t)nl->num_inputs + nl->num_gates;
   CK(P->wires.reserve(std::max<size_t>(wires, 1) * kWireStride * 4));
@@ -427,6 +450,9 @@ int plan_launch_levels(Engine &E, Plan &P, cudaStream_t st) {
     k.n = P.n;
     k.out = P.wires.as<uint32_t>();
     k.out_stride = kWireStride;
+    k.splits = L.ks_splits;
+    k.partial = P.kspart.as<uint32_t>();
+    k.counters = P.kscnt.as<unsigned int>();
     CK(launch_ks(k, L.ks_cnt, st));
   }
   return ARX_OK;
@@ -552,6 +578,11 @@ int bootstrap_gates(Engine &E, const uint8_t *types, const uint32_t *a, const ui
   k.n = ks->n;
   k.out = dev_out ? out : W.out.as<uint32_t>();
   k.out_stride = (int)row;
+  k.splits = ks_splits((int)count, E.sms);
+  rc = reserve_ks_scratch(W.kspart, W.kscnt, count, k.splits);
+  if (rc) return rc;
+  k.partial = W.kspart.as<uint32_t>();
+  k.counters = W.kscnt.as<unsigned int>();
   CK(launch_ks(k, (int)count, st));
   if (!dev_out) CK(cudaMemcpyAsync(out, W.out.p, count * row * 4, cudaMemcpyDeviceToHost, st));
   if (!user_st) return read_status(E, st);
@@ -831,6 +862,9 @@ extern "C" int arx_plan_profile(int plan, const uint32_t *ct_in, float *br_ms, f
     k.n = P.n;
     k.out = P.wires.as<uint32_t>();
     k.out_stride = kWireStride;
+    k.splits = L.ks_splits;
+    k.partial = P.kspart.as<uint32_t>();
+    k.counters = P.kscnt.as<unsigned int>();
     CK(launch_ks(k, L.ks_cnt, st));
     if (L.ks_cnt) ++nk;
     CK(cudaEventRecord(ev[4 * l + 3], st));

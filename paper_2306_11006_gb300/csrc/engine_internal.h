@@ -34,13 +34,14 @@ struct Keyset {
 };
 
 struct Workspace {
-  DevBuf wires, brjobs, ksjobs, brout, out;
+  DevBuf wires, brjobs, ksjobs, brout, out, kspart, kscnt;
 };
 
 struct Level {
   int br_off = 0, br_cnt = 0, ks_off = 0, ks_cnt = 0;
   BrShape shape{1, 1};
   int grid = 1;
+  int ks_splits = 1;
 };
 
 struct Plan {
@@ -49,7 +50,7 @@ struct Plan {
   std::vector<uint32_t> outputs;
   std::vector<Level> levels;
   uint64_t bootstraps = 0;
-  DevBuf wires, brjobs, ksjobs, brout, outidx, outstage;
+  DevBuf wires, brjobs, ksjobs, brout, outidx, outstage, kspart, kscnt;
   cudaGraphExec_t exec = nullptr;
 };
 
@@ -96,5 +97,6 @@ int grid_for(Engine &E, BrShape s, int jobs);
 int calibrate(Engine &E, int n);
 int levelize(const arx_netlist *nl, uint32_t *wave, uint32_t *depth);
 size_t keyset_bytes(int n);
+int reserve_ks_scratch(DevBuf &part, DevBuf &cnt, size_t jobs, int splits);
 
 }  // namespace arx

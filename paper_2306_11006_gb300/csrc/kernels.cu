@@ -71,60 +71,107 @@ __global__ void bsk_to_ntt_kernel(const uint32_t *__restrict__ bsk, int n, uint3
 }
 
 // ---------------------------------------------------------------------------
-// Key switch as a coalesced gather-accumulate: one CTA per gate, thread t owning
-// output words t, t+128, ...; for each of the N x t (i, j) pairs the CTA reads
-// the selected 632-word key row once.  The MUX sum (two extracted samples plus
-// 1/8) and the linear gates are folded in.
+// Key switch as a coalesced gather-accumulate (Fig. 2 "KeySwitch (Accum)"):
+// out = (0, ..., 0, b') - sum_i sum_j KSK[i][j][digit_ij].  A gate's N x t = 8192
+// key rows are split over `splits` CTAs (narrow waves spread one gate over many
+// SMs); thread t owns output words 4t .. 4t+3 and reads them with 128-bit loads,
+// two input coefficients (16 rows) in flight per iteration.  With splits > 1
+// each CTA writes its partial sum to scratch; the CTA that finishes last (per-gate
+// atomic counter, no waiting) adds the partials, writes the output and re-arms the
+// counter.  The MUX sum (two extracted samples plus 1/8) and the linear gates are
+// folded in.
 // ---------------------------------------------------------------------------
-constexpr int kKsThreads = 128;
-constexpr int kKsPer = (kMaxLweN + 1 + kKsThreads - 1) / kKsThreads;  // 5
+constexpr int kKsThreads = 160;             // 160 x 4 words >= 632
+constexpr int kKsVec = kKsRowStride / 4;    // 158 uint4 per row
 
 __global__ void __launch_bounds__(kKsThreads) ks_kernel(const __grid_constant__ KsArgs args) {
   __shared__ uint32_t lwe[kN + 1];
-  const KsJob jb = args.jobs[blockIdx.x];
+  __shared__ int last;
+  const int S = args.splits;
+  const int gate = blockIdx.x / S, split = blockIdx.x - gate * S;
+  const KsJob jb = args.jobs[gate];
   const int n = args.n;
   const int t = threadIdx.x;
   uint32_t *dst = args.out + (size_t)jb.out * args.out_stride;
-  if (jb.type == kGateNot || jb.type == kGateCopy) {
+  if (jb.type == kGateNot || jb.type == kGateCopy || jb.type == kGateConst0 || jb.type == kGateConst1) {
+    if (split) return;
     const uint32_t *src = args.wires + (size_t)jb.ia * kWireStride;
-    for (int k = t; k <= n; k += kKsThreads) dst[k] = jb.type == kGateNot ? 0u - src[k] : src[k];
+    for (int k = t; k <= n; k += kKsThreads) {
+      uint32_t v;
+      if (jb.type == kGateNot) v = 0u - src[k];
+      else if (jb.type == kGateCopy) v = src[k];
+      else v = k < n ? 0u : (jb.type == kGateConst1 ? kMu : 0u - kMu);
+      dst[k] = v;
+    }
     return;
   }
-  if (jb.type == kGateConst0 || jb.type == kGateConst1) {
-    for (int k = t; k <= n; k += kKsThreads) dst[k] = k < n ? 0u : (jb.type == kGateConst1 ? kMu : 0u - kMu);
-    return;
-  }
+  const int i0 = split * (kN / S), i1 = i0 + kN / S;
   const uint32_t *s0 = args.br_out + (size_t)jb.j0 * kOutStride;
-  if (jb.type == kGateMux) {
-    const uint32_t *s1 = args.br_out + (size_t)jb.j1 * kOutStride;
-    for (int k = t; k <= kN; k += kKsThreads) lwe[k] = s0[k] + s1[k] + (k == kN ? kMu : 0u);
-  } else {
-    for (int k = t; k <= kN; k += kKsThreads) lwe[k] = s0[k];
-  }
+  const uint32_t *s1 = args.br_out + (size_t)jb.j1 * kOutStride;
+  const bool mux = jb.type == kGateMux;
+  for (int k = i0 + t; k < i1; k += kKsThreads) lwe[k] = mux ? s0[k] + s1[k] : s0[k];
+  if (t == 0) lwe[kN] = mux ? s0[kN] + s1[kN] + kMu : s0[kN];
   __syncthreads();
-  uint32_t acc[kKsPer];
-#pragma unroll
-  for (int m = 0; m < kKsPer; ++m) acc[m] = (t + m * kKsThreads == n) ? lwe[kN] : 0u;
-  const uint32_t *__restrict__ ksk = args.ksk;
+  uint4 acc = make_uint4(0u, 0u, 0u, 0u);
+  if (split == 0 && 4 * t <= n && n < 4 * t + 4) {
+    const uint32_t b = lwe[kN];
+    if (n == 4 * t) acc.x = b; else if (n == 4 * t + 1) acc.y = b; else if (n == 4 * t + 2) acc.z = b; else acc.w = b;
+  }
+  const bool live = t < kKsVec;
+  const uint4 *__restrict__ ksk = reinterpret_cast<const uint4 *>(args.ksk);
 #pragma unroll 1
-  for (int i = 0; i < kN; ++i) {
-    const uint32_t y = lwe[i] + (1u << 15);  // round to 16 bits
+  for (int i = i0; i < i1; i += 2) {
+    uint4 r[16];
 #pragma unroll
-    for (int j = 1; j <= 8; ++j) {
-      const uint32_t v = (y >> (32 - 2 * j)) & 3u;
-      const uint32_t *row = ksk + ((size_t)(i * 8 + (j - 1)) * 3 + (v ? v - 1 : 0)) * kKsRowStride;
+    for (int u = 0; u < 2; ++u) {
+      const uint32_t y = lwe[i + u] + (1u << 15);  // round to 16 bits
 #pragma unroll
-      for (int m = 0; m < kKsPer; ++m) {
-        const int k = t + m * kKsThreads;
-        if (k <= n && v) acc[m] -= __ldg(row + k);
+      for (int j = 1; j <= 8; ++j) {
+        const uint32_t v = (y >> (32 - 2 * j)) & 3u;
+        const size_t row = ((size_t)((i + u) * 8 + (j - 1)) * 3 + (v ? v - 1 : 0)) * kKsVec;
+        r[u * 8 + j - 1] = (live && v) ? __ldg(ksk + row + t) : make_uint4(0u, 0u, 0u, 0u);
       }
     }
-  }
 #pragma unroll
-  for (int m = 0; m < kKsPer; ++m) {
-    const int k = t + m * kKsThreads;
-    if (k <= n) dst[k] = acc[m];
+    for (int q = 0; q < 16; ++q) {
+      acc.x -= r[q].x;
+      acc.y -= r[q].y;
+      acc.z -= r[q].z;
+      acc.w -= r[q].w;
+    }
   }
+  if (S == 1) {
+    if (live) {
+      if (4 * t + 0 <= n) dst[4 * t + 0] = acc.x;
+      if (4 * t + 1 <= n) dst[4 * t + 1] = acc.y;
+      if (4 * t + 2 <= n) dst[4 * t + 2] = acc.z;
+      if (4 * t + 3 <= n) dst[4 * t + 3] = acc.w;
+    }
+    return;
+  }
+  uint4 *part = reinterpret_cast<uint4 *>(args.partial) + (size_t)gate * S * kKsVec;
+  if (live) part[(size_t)split * kKsVec + t] = acc;
+  __threadfence();
+  __syncthreads();
+  if (t == 0) last = atomicAdd(args.counters + gate, 1u) == (unsigned)(S - 1);
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (live) {
+    uint4 sum = make_uint4(0u, 0u, 0u, 0u);
+    for (int q = 0; q < S; ++q) {
+      const uint4 v = __ldcg(part + (size_t)q * kKsVec + t);
+      sum.x += v.x;
+      sum.y += v.y;
+      sum.z += v.z;
+      sum.w += v.w;
+    }
+    if (4 * t + 0 <= n) dst[4 * t + 0] = sum.x;
+    if (4 * t + 1 <= n) dst[4 * t + 1] = sum.y;
+    if (4 * t + 2 <= n) dst[4 * t + 2] = sum.z;
+    if (4 * t + 3 <= n) dst[4 * t + 3] = sum.w;
+  }
+  if (t == 0) args.counters[gate] = 0u;
 }
 
 __global__ void gather_kernel(const uint32_t *__restrict__ wires, const uint32_t *__restrict__ idx, int count,
@@ -145,9 +192,18 @@ cudaError_t launch_bsk_to_ntt(const uint32_t *bsk_coef, int n, uint32_t *bsk_ntt
   return cudaGetLastError();
 }
 
+int ks_splits(int num_jobs, int sms) {
+  // aim at about four CTAs per SM; splits divide N and stay in 1..64
+  int s = 1;
+  while (s < 64 && (long long)num_jobs * s < 4LL * sms) s *= 2;
+  return s;
+}
+
 cudaError_t launch_ks(const KsArgs &args, int num_jobs, cudaStream_t st) {
   if (num_jobs <= 0) return cudaSuccess;
-  ks_kernel<<<num_jobs, kKsThreads, 0, st>>>(args);
+  if (args.splits < 1 || args.splits > 64 || (kN % args.splits) || (args.splits > 1 && (!args.partial || !args.counters)))
+    return cudaErrorInvalidValue;
+  ks_kernel<<<num_jobs * args.splits, kKsThreads, 0, st>>>(args);
   return cudaGetLastError();
 }
 
