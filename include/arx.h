@@ -169,6 +169,29 @@ int arx_plan_profile(int plan, const uint32_t *ct_in, float *br_ms, float *ks_ms
  * chosen when they were created. */
 int arx_set_launch_shape(int H, int GT);
 
+/* Key switch without allocation.  For callers that cannot allocate device
+ * memory during the call -- a serving process that budgets all of its HBM up
+ * front, a framework whose caching allocator must own every device buffer, or a
+ * latency-critical loop in which cudaMalloc / cudaFree would synchronise the
+ * device and stall other streams.  (The paper has no counterpart; this is a
+ * library service.)
+ *
+ * Key-switches count LWE_N samples lwe_N [count][N+1] (device memory, e.g.
+ * blind-rotation outputs) into LWE_n ciphertexts ct_out [count][n+1] (device
+ * memory) with a loaded key set (-1 = default), exactly as the gate path does.
+ * It calls no cudaMalloc, cudaFree or allocating library routine: the kernel's
+ * scratch (partial sums of the split key-row gather and one counter per gate)
+ * is a fixed static device array of about 2.6 MB that every GPU loading the
+ * library holds until the process exits.  count <= ARX_KS_NOALLOC_MAX, else
+ * ARX_EINVAL.  The first call on a device resolves the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call before
+ * any stream capture.  All calls share the array and each one clears the
+ * counters it uses, so calls that overlap on the GPU (different streams, or
+ * concurrent host threads) race: order them on one stream.  stream NULL means
+ * synchronous on the library's stream.  A key set must be loaded first. */
+#define ARX_KS_NOALLOC_MAX 1024
+int arx_keyswitch_noalloc(const uint32_t *lwe_N, uint32_t *ct_out, size_t count, int keyset, void *stream);
+
 /* ------------------------------------------------------------- status ---- */
 
 const char *arx_last_error(void);

@@ -53,6 +53,7 @@ SIGNATURES = {
     "arx_plan_wires": (_i, [_i, _vp, _sz, _vp]),
     "arx_set_launch_shape": (_i, [_i, _i]),
     "arx_plan_profile": (_i, [_i, _vp, _vp, _vp, _vp, _vp]),
+    "arx_keyswitch_noalloc": (_i, [_vp, _vp, _sz, _i, _vp]),
     "arx_last_error": (ctypes.c_char_p, []),
     "arx_device_status": (_i, []),
     "arx_device_sms": (_i, []),
@@ -220,6 +221,16 @@ class Plan:
 
     def __exit__(self, *exc):
         self.close()
+
+
+KS_NOALLOC_MAX = 1024
+
+
+def keyswitch_noalloc(lwe_N, ct_out, count=None, keyset: int = -1, stream=None) -> None:
+    """Key switch of LWE_N samples into LWE_n ciphertexts (device tensors) with no
+    device allocation inside the call (see include/arx.h)."""
+    count = len(lwe_N) if count is None else count
+    _check(lib().arx_keyswitch_noalloc(_ptr(lwe_N), _ptr(ct_out), count, keyset, _stream(stream)))
 
 
 def set_launch_shape(H: int = 0, GT: int = 0) -> None:
