@@ -51,15 +51,16 @@ MODMUL_PER_CMUX = 2 * (8 * 5120 + 12 * 1024)
 ALU_PEAK_TMODMUL = 152 * 2.070e9 * 64 / 3 / 1e12
 
 
-def workload(name: str):
+def workload(name: str, gates: int = 64):
     if name == "netlists":
         return I.union([I.ripple_carry_adder(32), I.array_multiplier(8)], name="adder32+mult8"), \
             "32-bit ripple-carry adder + 8x8 array multiplier (plain netlists, one wave per launch)"
-    if name == "gates64":
-        t = I.random_gate_types(1, 64)
-        nl = I.Netlist(128, t, np.arange(64, dtype=np.uint32), np.arange(64, 128, dtype=np.uint32),
-                       np.zeros(64, np.uint32), np.arange(128, 192, dtype=np.uint32), "gates64")
-        return nl, "64 independent 2-input gates (one wave)"
+    if name in ("gates", "gates64"):
+        g = gates
+        t = I.random_gate_types(1, g)
+        nl = I.Netlist(2 * g, t, np.arange(g, dtype=np.uint32), np.arange(g, 2 * g, dtype=np.uint32),
+                       np.zeros(g, np.uint32), np.arange(2 * g, 3 * g, dtype=np.uint32), f"gates{g}")
+        return nl, f"{g} independent 2-input gates (one wave)"
     if name == "dag":
         return I.random_dag(seed=3), "random levelized DAG, 65,536 gates over 40 waves, 5% MUX"
     if name == "matmul":
@@ -162,17 +163,130 @@ def run_reference(args, nl, desc):
     print(json.dumps(line), flush=True)
 
 
+def serve_request_pool(count: int, clients: int, seed: int = 5):
+    """Seeded request mix: 32-bit adder, 8x8 multiplier, 16-bit comparator, random
+    DAG with a log-uniform gate count in [1k, 50k]; client c = request % clients."""
+    rng = np.random.default_rng(seed)
+    pool = []
+    for r in range(count):
+        kind = int(rng.integers(0, 4))
+        if kind == 0:
+            nl = I.ripple_carry_adder(32)
+        elif kind == 1:
+            nl = I.array_multiplier(8)
+        elif kind == 2:
+            nl = I.comparator(16)
+        else:
+            g = int(np.exp(rng.uniform(np.log(1000), np.log(50000))))
+            levels = 20
+            wmin = max(8, g // 80)
+            wmax = max(2 * wmin, g // 8)
+            g = min(max(g, wmin * levels), wmax * levels)
+            nl = I.random_dag(seed=1000 + r, total=g, levels=levels, num_inputs=max(64, g // 20), wmin=wmin,
+                              wmax=wmax)
+        pool.append((r % clients, nl))
+    return pool
+
+
+def run_serve(args):
+    import torch
+
+    from paper_2306_11006_gb300 import arx
+
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    torch.cuda.set_device(local)
+    n = LWE_N
+    keys = []
+    for c in range(args.clients):
+        kr = I.key_randomness(100 + c, n)
+        bsk, ksk = arx.client_keygen(kr)
+        keys.append((kr, arx.load_keys(bsk, ksk, n)))
+    pool = serve_request_pool(args.requests, args.clients)
+    inputs = []
+    for r, (c, nl) in enumerate(pool):
+        bits = I.random_bits(7000 + r, nl.num_inputs)
+        m, e = I.encryption_randomness(8000 + r, nl.num_inputs, n)
+        inputs.append((bits, arx.client_encrypt(n, keys[c][0].s, m, e, bits)))
+    srv = arx.Server(hbm_budget=0, arena_bytes=4 << 30)
+    # warm-up: one small request per client (also triggers shape calibration)
+    warm = [srv.submit(I.comparator(4), arx.client_encrypt(n, keys[c][0].s, *I.encryption_randomness(1, 8, n),
+                                                           I.random_bits(1, 8)), keyset=keys[c][1])
+            for c in range(args.clients)]
+    for w in warm:
+        srv.wait(w)
+    base = srv.stats()
+    rng = np.random.default_rng(9)
+    arrivals = np.cumsum(rng.exponential(1.0 / args.rate, len(pool)))
+    clocks = Clocks(local, os.path.join(ROOT, "gpurun_out", "clocks_serve.csv")) \
+        if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else Clocks(local, "/tmp/arx_clocks_serve.csv")
+    ids = []
+    t0 = time.perf_counter()
+    for (c, nl), (bits, ct), at in zip(pool, inputs, arrivals):
+        delay = t0 + at - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        ids.append(srv.submit(nl, ct, keyset=keys[c][1]))
+    outs = [srv.wait(i) for i in ids]
+    elapsed = time.perf_counter() - t0
+    clk = clocks.stop()
+    st = srv.stats()
+    srv.stop()
+    ok = all(np.array_equal(arx.client_decrypt(n, keys[c][0].s, o), nl.plain_eval(b))
+             for (c, nl), (b, _), o in zip(pool, inputs, outs))
+    boots = st["bootstraps"] - base["bootstraps"]
+    gates = st["gates"] - base["gates"]
+    busy = st["busy_s"] - base["busy_s"]
+    achieved = boots * n * MODMUL_PER_CMUX / max(busy, 1e-9) / 1e12
+    line = {
+        "metric": METRIC, "value": boots / elapsed, "unit": "bootstraps/s", "n_gpus": world,
+        "steps": len(pool), "warmup": len(warm), "ms_per_step": 1e3 * elapsed / len(pool),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": f"serving: {args.clients} clients, Poisson {args.rate}/s, {len(pool)} requests "
+                               "(adder32 | mult8 | cmp16 | random DAG 1k-50k gates)", "lwe_n": n,
+                   "arrival_rate": args.rate, "clients": args.clients},
+        "latency_ms": {"p50": st["p50_ms"], "p99": st["p99_ms"]},
+        "gates_per_s": gates / elapsed, "verified": bool(ok),
+        "serve": {"requests": len(pool), "bootstraps": int(boots), "gates": int(gates), "elapsed_s": elapsed,
+                  "busy_s": busy, "ticks": int(st["ticks"] - base["ticks"]), "launches": int(st["launches"] - base["launches"]),
+                  "peak_active": int(st["peak_active"])},
+        "e2e": {"value": boots / elapsed, "unit": "bootstraps/s",
+                "h2d_bytes_per_step": int(np.mean([nl.num_inputs for _, nl in pool]) * (n + 1) * 4),
+                "d2h_bytes_per_step": int(np.mean([len(nl.outputs) for _, nl in pool]) * (n + 1) * 4)},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TMODMUL, "unit": "Tmodmul/s",
+                     "frac": achieved / ALU_PEAK_TMODMUL, "traffic": None,
+                     "kernel": "br_kernel + ks_kernel over the server's busy time"},
+        "gpu_launches": int(st["launches"] - base["launches"]),
+        "clocks": clk,
+    }
+    for _, ks in keys:
+        arx.unload_keys(ks)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="arx", choices=["arx", "reference"])
-    ap.add_argument("--workload", default="netlists", choices=["netlists", "gates64", "dag", "matmul"])
+    ap.add_argument("--workload", default="netlists", choices=["netlists", "gates", "gates64", "dag", "matmul", "serve"])
+    ap.add_argument("--clients", type=int, default=4, help="serve: clients (key sets)")
+    ap.add_argument("--rate", type=float, default=4.0, help="serve: Poisson arrival rate, requests/s")
+    ap.add_argument("--requests", type=int, default=32, help="serve: requests per run")
+    ap.add_argument("--gates", type=int, default=64, help="gate count of the independent-gates workload")
+    ap.add_argument("--shape", default=None, help="force the blind-rotation launch shape H,GT")
     ap.add_argument("--mode", default="graph", choices=["graph", "plain"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
-    nl, desc = workload(args.workload)
+    if args.workload == "serve":
+        if args.impl == "reference":
+            nl, desc = workload("dag")
+            return run_reference(args, nl, "serving request mix (oracle on its gate types)")
+        return run_serve(args)
+    nl, desc = workload(args.workload, args.gates)
     if args.impl == "reference":
         return run_reference(args, nl, desc)
 
@@ -201,6 +315,9 @@ def main():
     ct_in = torch.from_numpy(ct_host.view(np.int32)).to(dev)
     out = torch.zeros((len(nl.outputs), n + 1), dtype=torch.int32, device=dev)
     mode = arx.MODE_GRAPH if args.mode == "graph" else arx.MODE_PLAIN
+    if args.shape:
+        H, GT = (int(v) for v in args.shape.split(","))
+        arx.set_launch_shape(H, GT)
     plan = arx.Plan(nl, keyset=keyset, mode=mode)
     boots = plan.bootstraps
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -258,7 +375,7 @@ def main():
         "metric": METRIC, "value": value, "unit": "bootstraps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": desc, "lwe_n": n, "N": 1024, "mode": args.mode, "gates": nl.num_gates,
+        "config": {"workload": desc, "lwe_n": n, "N": 1024, "mode": args.mode, "shape": args.shape, "gates": nl.num_gates,
                    "bootstraps_per_step": boots, "waves": plan.waves,
                    "l2": "flushed between steps (256 MiB write)", "parallelism": "replicas" if world > 1 else "1 GPU"},
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},

@@ -93,6 +93,8 @@ int arx_use_keys(int keyset);
 
 /* Device bytes held by one key set of dimension lwe_n (NTT-domain BSK + KSK). */
 size_t arx_keyset_bytes(int lwe_n);
+/* Device bytes held by all key sets loaded now. */
+size_t arx_resident_bytes(void);
 
 /* ------------------------------------------------------------ gates ---- */
 
@@ -168,6 +170,39 @@ int arx_plan_profile(int plan, const uint32_t *ct_in, float *br_ms, float *ks_ms
  * (6,1) (3,1) (3,2) (2,1) (2,3) (1,1) (1,2) (1,4) (1,6).  Plans keep the shapes
  * chosen when they were created. */
 int arx_set_launch_shape(int H, int GT);
+
+/* ------------------------------------------------------------ serving ---- */
+/* Continuous batching of encrypted-circuit requests from several clients.
+ * arx_serve_start launches a scheduler thread with a wire arena of
+ * wire_arena_bytes of device memory and an HBM budget (bytes of resident key
+ * sets + wires of admitted requests; 0 = no budget).  Requests are admitted in
+ * arrival order while their wires fit the budget and the arena; every scheduler
+ * tick advances each admitted request by one wave, with the waves of all
+ * requests on the same key set merged into one blind-rotation and one
+ * key-switch launch (at most max_tick_bootstraps blind rotations per launch,
+ * 0 = no cap; one request always runs).  Requests arriving meanwhile join at the
+ * next tick.  A request's result is bit-identical to arx_eval_netlist's on the
+ * same inputs, whatever else is in flight. */
+typedef struct {
+  uint64_t completed, failed, gates, bootstraps, launches, ticks;
+  uint64_t pending, active, peak_active, peak_bytes;
+  double p50_ms, p99_ms;  /* submit-to-completion latency of completed requests */
+  double busy_s, elapsed_s;
+} arx_serve_info;
+
+int arx_serve_start(size_t hbm_budget_bytes, size_t wire_arena_bytes, uint32_t max_tick_bootstraps);
+/* Queue a request: netlist and inputs (host memory) are copied, so the caller may
+ * free them on return; ct_out (host, [num_outputs][n+1]) is written when the
+ * request completes.  Returns a request id >= 0 or an error (bad netlist, no key
+ * set, larger than the budget or the arena). */
+int arx_serve_submit(int keyset, const arx_netlist *nl, const uint32_t *ct_in, uint32_t *ct_out);
+/* 1 = done, 0 = pending, < 0 = failed. */
+int arx_serve_poll(int request);
+/* Wait up to timeout_s seconds: 1 = done, 0 = still pending, < 0 = failed. */
+int arx_serve_wait(int request, double timeout_s);
+int arx_serve_stats(arx_serve_info *out);
+/* Finish every queued request, then stop the scheduler. */
+int arx_serve_stop(void);
 
 /* Key switch without allocation.  For callers that cannot allocate device
  * memory during the call -- a serving process that budgets all of its HBM up

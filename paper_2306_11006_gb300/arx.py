@@ -29,6 +29,12 @@ STATUS = {0: "ARX_OK", -1: "ARX_EINVAL", -2: "ARX_ENOKEYS", -3: "ARX_ENOMEM", -4
 _vp, _sz, _i, _u32, _u64 = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_uint32, ctypes.c_uint64
 
 
+class ServeStats_C(ctypes.Structure):
+    _fields_ = [(k, _u64) for k in ("completed", "failed", "gates", "bootstraps", "launches", "ticks", "pending",
+                                    "active", "peak_active", "peak_bytes")] + \
+               [(k, ctypes.c_double) for k in ("p50_ms", "p99_ms", "busy_s", "elapsed_s")]
+
+
 class Netlist_C(ctypes.Structure):
     _fields_ = [("num_inputs", _u32), ("num_gates", _u32), ("num_outputs", _u32), ("type", _vp),
                 ("in0", _vp), ("in1", _vp), ("in2", _vp), ("outputs", _vp)]
@@ -41,6 +47,7 @@ SIGNATURES = {
     "arx_unload_keys": (_i, [_i]),
     "arx_use_keys": (_i, [_i]),
     "arx_keyset_bytes": (_sz, [_i]),
+    "arx_resident_bytes": (_sz, []),
     "arx_bootstrap_gates": (_i, [_vp, _vp, _vp, _vp, _sz]),
     "arx_bootstrap_gates_ex": (_i, [_vp, _vp, _vp, _vp, _vp, _sz, _i, _vp]),
     "arx_levelize": (_i, [_NLP, _vp, _vp]),
@@ -54,6 +61,12 @@ SIGNATURES = {
     "arx_set_launch_shape": (_i, [_i, _i]),
     "arx_plan_profile": (_i, [_i, _vp, _vp, _vp, _vp, _vp]),
     "arx_keyswitch_noalloc": (_i, [_vp, _vp, _sz, _i, _vp]),
+    "arx_serve_start": (_i, [_sz, _sz, _u32]),
+    "arx_serve_submit": (_i, [_i, _NLP, _vp, _vp]),
+    "arx_serve_poll": (_i, [_i]),
+    "arx_serve_wait": (_i, [_i, ctypes.c_double]),
+    "arx_serve_stats": (_i, [ctypes.POINTER(ServeStats_C)]),
+    "arx_serve_stop": (_i, []),
     "arx_last_error": (ctypes.c_char_p, []),
     "arx_device_status": (_i, []),
     "arx_device_sms": (_i, []),
@@ -127,6 +140,11 @@ def load_keys(bsk, ksk, lwe_n: int = LWE_N, stream=None) -> int:
 
 def unload_keys(keyset: int) -> None:
     _check(lib().arx_unload_keys(keyset))
+
+
+def resident_bytes() -> int:
+    """Device bytes held by all loaded key sets."""
+    return int(lib().arx_resident_bytes())
 
 
 def use_keys(keyset: int) -> None:
@@ -231,6 +249,47 @@ def keyswitch_noalloc(lwe_N, ct_out, count=None, keyset: int = -1, stream=None) 
     device allocation inside the call (see include/arx.h)."""
     count = len(lwe_N) if count is None else count
     _check(lib().arx_keyswitch_noalloc(_ptr(lwe_N), _ptr(ct_out), count, keyset, _stream(stream)))
+
+
+class Server:
+    """Continuous-batching server (arx_serve_*): submit netlist requests from any
+    number of clients (key sets); results arrive in the caller's host buffers."""
+
+    def __init__(self, hbm_budget: int = 0, arena_bytes: int = 1 << 30, max_tick_bootstraps: int = 0):
+        _check(lib().arx_serve_start(hbm_budget, arena_bytes, max_tick_bootstraps))
+        self._keep = {}
+
+    def submit(self, nl, ct_in, keyset: int = -1, n: int = LWE_N):
+        r = _NetlistRef(nl)
+        ct_in = np.ascontiguousarray(np.asarray(ct_in, dtype=np.uint32))
+        out = np.zeros((len(r.outputs), n + 1), np.uint32)
+        rid = _check(lib().arx_serve_submit(keyset, r.ref, _ptr(ct_in), _ptr(out)))
+        self._keep[rid] = out
+        return rid
+
+    def poll(self, rid: int) -> int:
+        return lib().arx_serve_poll(rid)
+
+    def wait(self, rid: int, timeout_s: float = 600.0):
+        """Block until request rid completes; returns its output ciphertexts."""
+        rc = _check(lib().arx_serve_wait(rid, timeout_s))
+        if rc != 1:
+            raise TimeoutError(f"request {rid} still pending after {timeout_s} s")
+        return self._keep.pop(rid)
+
+    def stats(self) -> dict:
+        st = ServeStats_C()
+        _check(lib().arx_serve_stats(ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in ServeStats_C._fields_}
+
+    def stop(self) -> None:
+        _check(lib().arx_serve_stop())
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.stop()
 
 
 def set_launch_shape(H: int = 0, GT: int = 0) -> None:

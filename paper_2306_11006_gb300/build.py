@@ -20,7 +20,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libarx.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU = ["br_h1.cu", "br_h2.cu", "br_h3.cu", "br_h6.cu", "kernels.cu", "noalloc.cu"]
-CPP = ["engine.cpp", "twiddles.cpp", "client.cpp"]
+CPP = ["engine.cpp", "serve.cpp", "twiddles.cpp", "client.cpp"]
 
 
 def nvcc() -> str:

@@ -79,6 +79,7 @@ int ensure_init(Engine &E) {
   if (prop.major < 10)
     return fail(ARX_ECUDA, "device %s (sm_%d%d): libarx is built for sm_103a", prop.name, prop.major, prop.minor);
   E.sms = prop.multiProcessorCount;
+  E.policy.sms = E.sms;
   E.smem_optin = prop.sharedMemPerBlockOptin;
   std::unique_ptr<TwiddleGlobal> tg(new TwiddleGlobal);
   make_twiddles(&E.tc, tg.get());
@@ -173,18 +174,18 @@ void emit_gate(uint32_t type, uint32_t w0, uint32_t w1, uint32_t w2, uint32_t ou
 // --------------------------------------------------------------------------
 const BrShape kShapes[] = {{6, 1}, {3, 1}, {3, 2}, {2, 1}, {2, 3}, {1, 1}, {1, 2}, {1, 4}, {1, 6}};
 
-int ctas_per_sm(Engine &E, BrShape s) {
-  for (auto &kv : E.occ)
+int ShapePolicy::occupancy(BrShape s) {
+  for (auto &kv : occ)
     if (kv.first.H == s.H && kv.first.GT == s.GT) return kv.second;
-  const int occ = br_occupancy(s);
-  E.occ.push_back({s, occ});
-  return occ;
+  const int o = br_occupancy(s);
+  occ.push_back({s, o});
+  return o;
 }
 
 // Plain mode: about twelve consumer warps per SM, more gates per CTA as the wave widens.
-BrShape heuristic_shape(Engine &E, int jobs) {
-  if (E.forced.H) return E.forced;
-  const int per_sm = (jobs + E.sms - 1) / E.sms;
+BrShape ShapePolicy::heuristic(int jobs) const {
+  if (forced.H) return forced;
+  const int per_sm = (jobs + sms - 1) / sms;
   if (per_sm <= 1) return {6, 1};
   if (per_sm == 2) return {3, 2};
   if (per_sm == 3) return {2, 3};
@@ -192,9 +193,26 @@ BrShape heuristic_shape(Engine &E, int jobs) {
   return {1, 6};
 }
 
-int grid_for(Engine &E, BrShape s, int jobs) {
+// Autotuned: the shape minimising waves x measured time per wave.
+BrShape ShapePolicy::pick(int jobs, int n) const {
+  if (forced.H) return forced;
+  if (tune.empty() || tuned_n != n) return heuristic(jobs);
+  double best = 1e300;
+  BrShape out = tune.front().shape;
+  for (const TuneEntry &t : tune) {
+    const int waves = (jobs + t.gates_per_wave - 1) / t.gates_per_wave;
+    const double cost = waves * t.wave_ms_per_cmux;
+    if (cost < best * 0.999) {
+      best = cost;
+      out = t.shape;
+    }
+  }
+  return out;
+}
+
+int ShapePolicy::grid(BrShape s, int jobs) {
   const int tiles = (jobs + s.GT - 1) / s.GT;
-  const int cap = E.sms * std::max(1, ctas_per_sm(E, s));
+  const int cap = sms * std::max(1, occupancy(s));
   return std::max(1, std::min(tiles, cap));
 }
 
@@ -202,10 +220,10 @@ int grid_for(Engine &E, BrShape s, int jobs) {
 // synthetic blind rotation (timing is data-independent), then pick the shape
 // minimising waves x time-per-wave for each launch width.
 int calibrate(Engine &E, int n) {
-  if (E.tuned_n == n) return ARX_OK;
+  if (E.policy.tuned_n == n) return ARX_OK;
   const int ncal = std::min(n, 16);
   int max_jobs = 0;
-  for (BrShape s : kShapes) max_jobs = std::max(max_jobs, E.sms * s.GT * std::max(1, ctas_per_sm(E, s)));
+  for (BrShape s : kShapes) max_jobs = std::max(max_jobs, E.sms * s.GT * std::max(1, E.policy.occupancy(s)));
   DevBuf bsk, wires, jobs, out;
   CK(bsk.reserve((size_t)ncal * 6 * kChunkBytes));
   CK(wires.reserve((size_t)kWireStride * 4 * 2));
@@ -218,20 +236,20 @@ int calibrate(Engine &E, int n) {
   cudaEvent_t a, b;
   CK(cudaEventCreate(&a));
   CK(cudaEventCreate(&b));
-  E.tune.clear();
+  E.policy.tune.clear();
   for (BrShape s : kShapes) {
-    if (!ctas_per_sm(E, s)) continue;
+    if (!E.policy.occupancy(s)) continue;
     BrArgs args{};
     args.bsk = bsk.as<uint32_t>();
     args.wires = wires.as<uint32_t>();
     args.jobs = jobs.as<BrJob>();
-    args.num_jobs = E.sms * s.GT * ctas_per_sm(E, s);
+    args.num_jobs = E.sms * s.GT * E.policy.occupancy(s);
     args.n = ncal;
     args.out = out.as<uint32_t>();
     args.tg = E.tg;
     args.status = E.status;
     args.tc = E.tc;
-    const int grid = grid_for(E, s, args.num_jobs);
+    const int grid = E.policy.grid(s, args.num_jobs);
     float best = 1e30f;
     for (int rep = 0; rep < 3; ++rep) {
       CK(cudaEventRecord(a, E.stream));
@@ -246,7 +264,7 @@ int calibrate(Engine &E, int n) {
     t.shape = s;
     t.wave_ms_per_cmux = best / ncal;
     t.gates_per_wave = args.num_jobs;
-    E.tune.push_back(t);
+    E.policy.tune.push_back(t);
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
@@ -256,24 +274,8 @@ int calibrate(Engine &E, int n) {
   out.release();
   int rc = read_status(E, E.stream);
   if (rc) return rc;
-  E.tuned_n = n;
+  E.policy.tuned_n = n;
   return ARX_OK;
-}
-
-BrShape tuned_shape(Engine &E, int jobs, int n) {
-  if (E.forced.H) return E.forced;
-  if (E.tune.empty() || E.tuned_n != n) return heuristic_shape(E, jobs);
-  double best = 1e300;
-  BrShape pick = E.tune.front().shape;
-  for (const TuneEntry &t : E.tune) {
-    const int waves = (jobs + t.gates_per_wave - 1) / t.gates_per_wave;
-    const double cost = waves * t.wave_ms_per_cmux;
-    if (cost < best * 0.999) {
-      best = cost;
-      pick = t.shape;
-    }
-  }
-  return pick;
 }
 
 // --------------------------------------------------------------------------
@@ -399,8 +401,8 @@ int plan_build(Engine &E, const arx_netlist *nl, int keyset, int mode, std::uniq
   }
   size_t ks_part_max = 0, ks_gate_max = 0;
   for (Level &L : P->levels) {
-    L.shape = mode == ARX_MODE_GRAPH ? tuned_shape(E, L.br_cnt, P->n) : heuristic_shape(E, L.br_cnt);
-    L.grid = grid_for(E, L.shape, std::max(1, L.br_cnt));
+    L.shape = mode == ARX_MODE_GRAPH ? E.policy.pick(L.br_cnt, P->n) : E.policy.heuristic(L.br_cnt);
+    L.grid = E.policy.grid(L.shape, std::max(1, L.br_cnt));
     L.ks_splits = ks_splits(L.ks_cnt, E.sms);
     if (L.ks_splits > 1) {
       ks_part_max = std::max(ks_part_max, (size_t)L.ks_cnt * L.ks_splits);
@@ -565,8 +567,8 @@ int bootstrap_gates(Engine &E, const uint8_t *types, const uint32_t *a, const ui
     args.tg = E.tg;
     args.status = E.status;
     args.tc = E.tc;
-    const BrShape s = E.tuned_n == ks->n ? tuned_shape(E, args.num_jobs, ks->n) : heuristic_shape(E, args.num_jobs);
-    CK(launch_br(args, s, grid_for(E, s, args.num_jobs), st));
+    const BrShape s = E.policy.pick(args.num_jobs, ks->n);
+    CK(launch_br(args, s, E.policy.grid(s, args.num_jobs), st));
   }
   const bool dev_out = is_device_ptr(out);
   if (!dev_out) CK(W.out.reserve(count * row * 4));
@@ -710,6 +712,12 @@ extern "C" int arx_use_keys(int keyset) {
   if (rc) return rc;
   E.last = keyset;
   return ARX_OK;
+}
+
+extern "C" size_t arx_resident_bytes(void) {
+  Engine &E = eng();
+  std::lock_guard<std::mutex> lk(E.mu);
+  return E.resident_bytes();
 }
 
 extern "C" size_t arx_keyset_bytes(int lwe_n) { return lwe_n < 1 || lwe_n > kMaxLweN ? 0 : keyset_bytes(lwe_n); }
@@ -890,11 +898,11 @@ extern "C" int arx_set_launch_shape(int H, int GT) {
   Engine &E = eng();
   std::lock_guard<std::mutex> lk(E.mu);
   if (H == 0 && GT == 0) {
-    E.forced = BrShape{0, 0};
+    E.policy.forced = BrShape{0, 0};
     return ARX_OK;
   }
   if (!br_shape_supported(BrShape{H, GT})) return fail(ARX_EINVAL, "unsupported launch shape (%d, %d)", H, GT);
-  E.forced = BrShape{H, GT};
+  E.policy.forced = BrShape{H, GT};
   return ARX_OK;
 }
 

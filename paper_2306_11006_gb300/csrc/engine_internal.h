@@ -60,6 +60,21 @@ struct TuneEntry {
   int gates_per_wave = 0;
 };
 
+// Launch-shape choice: the autotuned table (one LWE dimension), resident CTAs
+// per SM of every shape, and an optional override.  Copyable, so that the
+// serving thread can use a snapshot without the engine lock.
+struct ShapePolicy {
+  int sms = 0;
+  std::vector<TuneEntry> tune;
+  int tuned_n = -1;
+  std::vector<std::pair<BrShape, int>> occ;
+  BrShape forced{0, 0};
+  int occupancy(BrShape s);
+  BrShape heuristic(int jobs) const;
+  BrShape pick(int jobs, int n) const;
+  int grid(BrShape s, int jobs);
+};
+
 struct Engine {
   std::mutex mu;
   bool ready = false;
@@ -75,10 +90,7 @@ struct Engine {
   size_t budget = 0;  // HBM budget for resident keys (0 = none)
   std::map<cudaStream_t, Workspace> ws;
   std::vector<std::unique_ptr<Plan>> plans;
-  std::vector<TuneEntry> tune;
-  int tuned_n = -1;
-  std::vector<std::pair<BrShape, int>> occ;  // resident CTAs per SM of each shape
-  BrShape forced{0, 0};  // launch-shape override (H = 0: automatic)
+  ShapePolicy policy;
   size_t resident_bytes() const;
 };
 
@@ -91,9 +103,6 @@ int read_status(Engine &E, cudaStream_t st);
 int gate_arity(uint32_t type);
 void emit_gate(uint32_t type, uint32_t w0, uint32_t w1, uint32_t w2, uint32_t out, std::vector<BrJob> &br,
                std::vector<KsJob> &ks, uint32_t br_base);
-BrShape heuristic_shape(Engine &E, int jobs);
-BrShape tuned_shape(Engine &E, int jobs, int n);
-int grid_for(Engine &E, BrShape s, int jobs);
 int calibrate(Engine &E, int n);
 int levelize(const arx_netlist *nl, uint32_t *wave, uint32_t *depth);
 size_t keyset_bytes(int n);
