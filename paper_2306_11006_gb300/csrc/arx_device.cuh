@@ -3,18 +3,23 @@
 // Exact negacyclic polynomial products (Sec. 2.2: "TGSW BK_i x TLWE temp" of
 // Fig. 2) through number-theoretic transforms (Sec. 5.4 motivates the NTT over
 // the FFT because it is exact).  The paper's A100 design used one 64-bit prime;
-// here each product is carried modulo two 28-bit primes (CRT), so every modular
+// here each product is carried modulo two 27-bit primes (CRT), so every modular
 // multiply is a native 32-bit IMAD / IMAD.HI sequence:
-//   q0 = 195198977, q1 = 195188737, both = 1 (mod 2048), q0*q1 > 2^55,
+//   q0 = 134215681, q1 = 134203393, both = 1 (mod 2048), q0 q1 > 2^53,
 // while the exact products are bounded by 6 * 1024 * 64 * 2^31 < 2^50.
 //
 // Warp-per-transform layout: a 1024-point transform is held by one warp, 32
-// values per lane.  Pass 1 (lengths 512..32) runs on x[e] = a[lane + 32 e] with
-// warp-uniform twiddles read from the constant bank; a padded shared-memory
-// transpose moves lane to a[32 lane + e]; pass 2 (lengths 16..1) uses per-lane
-// twiddles.  The inverse runs the mirror image.  Values are kept lazily reduced:
-// the forward pass needs no correction at all (inputs < 2q, each stage adds < 2q,
-// 22 q < 2^32), the inverse uses Harvey's [0, 2q) Gentleman-Sande butterfly.
+// values per lane.  Forward (negacyclic Cooley-Tukey with merged twist, natural
+// order in, bit-reversed order out): pass 1 (lengths 512..32) on
+// x[e] = a[lane + 32 e] with warp-uniform twiddles from the kernel parameter bank,
+// a swizzled shared-memory transpose, pass 2 (lengths 16..1) on a[32 lane + e]
+// with per-lane twiddles.  Inverse (cyclic Cooley-Tukey DIT with omega^-1,
+// bit-reversed in, natural out, then the output twist psi^-j): pass 1 on
+// a[32 lane + e] with uniform twiddles, transpose, pass 2 with per-lane twiddles.
+// Both directions grow lazily by < 2q per stage with no correction: the forward
+// starts below 3q + 128 and ends below 22q, the inverse starts below 12q (six
+// Montgomery products) and ends below 32q < 2^32.  The twist's Shoup product and
+// one conditional subtraction bring the result to [0, q).
 #pragma once
 #include <cstdint>
 
@@ -22,11 +27,9 @@
 
 namespace arx {
 
-constexpr int kRows = 6;          // (k+1) l TGSW rows, l = 3
+constexpr int kRows = 6;               // (k+1) l TGSW rows, l = 3
 constexpr uint32_t kMu = 0x20000000u;  // +1/8
-constexpr int kPad = 33;                           // transpose row pitch (words)
-constexpr int kXpose = 32 * kPad;                  // 1056 words per transpose buffer
-
+constexpr int kXpose = 1024;           // words per transpose buffer (swizzled, unpadded)
 
 __host__ __device__ constexpr uint32_t neg_inv32(uint32_t q) {
   uint32_t x = q;  // correct to 3 bits for odd q; Newton doubles the bits
@@ -34,115 +37,138 @@ __host__ __device__ constexpr uint32_t neg_inv32(uint32_t q) {
   return 0u - x;
 }
 
-template <int P> struct Prime;
-template <> struct Prime<0> {
-  static constexpr uint32_t q = kQ0;
-  static constexpr uint32_t qneg_inv = neg_inv32(kQ0);
+// One CRT prime, in registers (the same code serves both primes).
+struct PrimeRT {
+  uint32_t q, q2, qni;  // q, 2q, -q^-1 mod 2^32
+  uint32_t dc, dd;      // first-stage offsets for raw digit bytes (see ntt_fwd)
 };
-template <> struct Prime<1> {
-  static constexpr uint32_t q = kQ1;
-  static constexpr uint32_t qneg_inv = neg_inv32(kQ1);
-};
+
+__device__ __forceinline__ PrimeRT prime_rt(int P, const TwiddleConst &tc) {
+  PrimeRT r;
+  r.q = P ? kQ1 : kQ0;
+  r.q2 = 2u * r.q;
+  r.qni = P ? neg_inv32(kQ1) : neg_inv32(kQ0);
+  r.dc = tc.dig_c[P];
+  r.dd = tc.dig_d[P];
+  return r;
+}
 
 // ---- modular helpers ----------------------------------------------------
 // Shoup: w * y mod q in [0, 2q) for any 32-bit y, given wp = floor(w 2^32 / q).
-template <int P>
-__device__ __forceinline__ uint32_t shoup_mul(uint32_t w, uint32_t wp, uint32_t y) {
-  uint32_t qhat = __umulhi(wp, y);
-  return w * y - qhat * Prime<P>::q;
+__device__ __forceinline__ uint32_t shoup_mul(uint32_t w, uint32_t wp, uint32_t y, uint32_t q) {
+  return w * y - __umulhi(wp, y) * q;
 }
 
 // Montgomery: a b 2^-32 mod q in [0, 2q) for a b < 2^32 q.
-template <int P>
-__device__ __forceinline__ uint32_t mont_mul(uint32_t a, uint32_t b) {
-  uint64_t t = (uint64_t)a * b;
-  uint32_t m = (uint32_t)t * Prime<P>::qneg_inv;
-  return (uint32_t)((t + (uint64_t)m * Prime<P>::q) >> 32);
+__device__ __forceinline__ uint32_t mont_mul(uint32_t a, uint32_t b, const PrimeRT &pr) {
+  const uint64_t t = (uint64_t)a * b;
+  const uint32_t m = (uint32_t)t * pr.qni;
+  return (uint32_t)((t + (uint64_t)m * pr.q) >> 32);
 }
 
 __device__ __forceinline__ uint32_t csub(uint32_t x, uint32_t m) { return min(x, x - m); }
 
-template <int P>
-__device__ __forceinline__ void ct_bfly(uint32_t &x, uint32_t &y, uint2 z) {
-  uint32_t t = shoup_mul<P>(z.x, z.y, y);
-  y = x - t + 2u * Prime<P>::q;
+__device__ __forceinline__ void ct_bfly(uint32_t &x, uint32_t &y, uint2 z, const PrimeRT &pr) {
+  const uint32_t t = shoup_mul(z.x, z.y, y, pr.q);
+  y = x - t + pr.q2;
   x = x + t;
 }
 
-template <int P>
-__device__ __forceinline__ void gs_bfly(uint32_t &x, uint32_t &y, uint2 z) {
-  uint32_t s = csub(x + y, 2u * Prime<P>::q);
-  uint32_t d = x - y + 2u * Prime<P>::q;
-  x = s;
-  y = shoup_mul<P>(z.x, z.y, d);
-}
+// Element (row r, column c) of a 32 x 32 transpose buffer: 16-byte chunks of a
+// row are XOR-swizzled by r & 7, so that a column write (32 lanes, one row) and a
+// 128-bit row read (8 lanes per wavefront, 8 rows) are both conflict-free.
+__device__ __forceinline__ int swz(int r, int c) { return r * 32 + ((((c >> 2) ^ (r & 7))) << 2) + (c & 3); }
 
 // ---- warp transforms ----------------------------------------------------
-// Forward: x[e] = a[lane + 32 e] with a < 2q  ->  x[e] = A[32 lane + e] < 22 q.
-template <int P>
-__device__ __forceinline__ void ntt_fwd(uint32_t (&x)[32], uint32_t *xbuf, const TwiddleConst &tc,
-                                        const uint2 *__restrict__ tw2, int lane) {
+// Forward.  kDigits: x[e] holds raw gadget digit bytes u = d + 64 in [0, 128) of
+// a[lane + 32 e]; the -64 offsets ride on the first stage's constants.
+// Otherwise x[e] < q.  Output: x[e] = A[32 lane + e] < 22 q.
+template <bool kDigits>
+__device__ __forceinline__ void ntt_fwd(uint32_t (&x)[32], uint32_t *xbuf, const uint2 *tw1,
+                                        const uint2 *__restrict__ tw2, const PrimeRT &pr, int lane) {
+  {
+    const uint2 z = tw1[1];
 #pragma unroll
-  for (int s = 0; s < 5; ++s) {
+    for (int e = 0; e < 16; ++e) {
+      if (kDigits) {
+        const uint32_t t = shoup_mul(z.x, z.y, x[e + 16], pr.q);
+        const uint32_t u = x[e];
+        x[e] = u + t + pr.dc;
+        x[e + 16] = u - t + pr.q2 + pr.dd;
+      } else {
+        ct_bfly(x[e], x[e + 16], z, pr);
+      }
+    }
+  }
+#pragma unroll
+  for (int s = 1; s < 5; ++s) {
     const int lr = 16 >> s;
 #pragma unroll
     for (int e = 0; e < 32; ++e) {
-      if ((e & lr) == 0) ct_bfly<P>(x[e], x[e + lr], tc.fwd1[P][(1 << s) + e / (2 * lr)]);
+      if ((e & lr) == 0) ct_bfly(x[e], x[e + lr], tw1[(1 << s) + e / (2 * lr)], pr);
     }
   }
   __syncwarp();
 #pragma unroll
-  for (int e = 0; e < 32; ++e) xbuf[lane + kPad * e] = x[e];
+  for (int e = 0; e < 32; ++e) xbuf[swz(e, lane)] = x[e];
   __syncwarp();
+  const uint4 *xb4 = reinterpret_cast<const uint4 *>(xbuf);
 #pragma unroll
-  for (int e = 0; e < 32; ++e) x[e] = xbuf[kPad * lane + e];
+  for (int c = 0; c < 8; ++c) {
+    const uint4 v = xb4[lane * 8 + (c ^ (lane & 7))];
+    x[4 * c + 0] = v.x;
+    x[4 * c + 1] = v.y;
+    x[4 * c + 2] = v.z;
+    x[4 * c + 3] = v.w;
+  }
 #pragma unroll
   for (int s = 0; s < 5; ++s) {
-    const int len = 16 >> s;       // 16, 8, 4, 2, 1
-    const int k0 = (1 << s) - 1;   // 0, 1, 3, 7, 15: first per-lane zeta of the stage
+    const int len = 16 >> s;      // 16, 8, 4, 2, 1
+    const int k0 = (1 << s) - 1;  // 0, 1, 3, 7, 15: first per-lane zeta of the stage
     uint2 z;
 #pragma unroll
     for (int e = 0; e < 32; ++e) {
       if ((e & len) == 0) {
         if ((e & (2 * len - 1)) == 0) z = __ldg(tw2 + (k0 + e / (2 * len)) * 32 + lane);
-        ct_bfly<P>(x[e], x[e + len], z);
+        ct_bfly(x[e], x[e + len], z, pr);
       }
     }
   }
 }
 
-// Inverse (without the 1/N factor, which the stored key carries):
-// x[e] = A[32 lane + e] < 2q  ->  x[e] = a[lane + 32 e] < 2q.
-template <int P>
-__device__ __forceinline__ void ntt_inv(uint32_t (&x)[32], uint32_t *xbuf, const TwiddleConst &tc,
-                                        const uint2 *__restrict__ tw1, int lane) {
+// Inverse (the 1/N factor rides on the stored key): x[e] = A[32 lane + e] < 12 q
+// -> x[e] = a[lane + 32 e] in [0, q).
+__device__ __forceinline__ void ntt_inv(uint32_t (&x)[32], uint32_t *xbuf, const uint2 *tw1,
+                                        const uint2 *__restrict__ tw2, const uint2 *__restrict__ twist,
+                                        const PrimeRT &pr, int lane) {
 #pragma unroll
   for (int t = 0; t < 5; ++t) {
-    const int len = 1 << t;        // 1, 2, 4, 8, 16
-    const int blocks = 16 >> t;    // 16, 8, 4, 2, 1
-    const int k0 = blocks - 1;     // 15, 7, 3, 1, 0
-    uint2 z;
+    const int h = 1 << t;  // half-length 1, 2, 4, 8, 16
 #pragma unroll
     for (int e = 0; e < 32; ++e) {
-      if ((e & len) == 0) {
-        if ((e & (2 * len - 1)) == 0) z = __ldg(tw1 + (k0 + e / (2 * len)) * 32 + lane);
-        gs_bfly<P>(x[e], x[e + len], z);
-      }
+      if ((e & h) == 0) ct_bfly(x[e], x[e + h], tw1[(h - 1) + (e & (h - 1))], pr);
     }
   }
   __syncwarp();
+  uint4 *xb4 = reinterpret_cast<uint4 *>(xbuf);
 #pragma unroll
-  for (int e = 0; e < 32; ++e) xbuf[kPad * lane + e] = x[e];
+  for (int c = 0; c < 8; ++c)
+    xb4[lane * 8 + (c ^ (lane & 7))] = make_uint4(x[4 * c], x[4 * c + 1], x[4 * c + 2], x[4 * c + 3]);
   __syncwarp();
 #pragma unroll
-  for (int e = 0; e < 32; ++e) x[e] = xbuf[lane + kPad * e];
+  for (int e = 0; e < 32; ++e) x[e] = xbuf[swz(e, lane)];
 #pragma unroll
-  for (int t = 0; t < 5; ++t) {
-    const int lr = 1 << t;  // 1, 2, 4, 8, 16: undoes forward pass-1 stage m = 16 >> t
+  for (int s = 0; s < 5; ++s) {
+    const int hr = 1 << s;  // half-length / 32: 1, 2, 4, 8, 16
 #pragma unroll
     for (int e = 0; e < 32; ++e) {
-      if ((e & lr) == 0) gs_bfly<P>(x[e], x[e + lr], tc.inv2[P][(16 >> t) + e / (2 * lr)]);
+      if ((e & hr) == 0) ct_bfly(x[e], x[e + hr], __ldg(tw2 + ((hr - 1) + (e & (hr - 1))) * 32 + lane), pr);
     }
+  }
+#pragma unroll
+  for (int e = 0; e < 32; ++e) {
+    const uint2 w = __ldg(twist + e * 32 + lane);
+    x[e] = csub(shoup_mul(w.x, w.y, x[e], pr.q), pr.q);
   }
 }
 

@@ -14,25 +14,28 @@ constexpr int kOutStride = 1028;  // words per extracted LWE_N sample
 constexpr int kKsRowStride = 632; // words per key-switching-key row
 constexpr int kChunkWords = 2 * 2 * kN;       // one BSK row: [c_out 2][prime 2][N]
 constexpr int kChunkBytes = kChunkWords * 4;  // 16 KiB
-constexpr uint32_t kQ0 = 195198977u;
-constexpr uint32_t kQ1 = 195188737u;
+constexpr uint32_t kQ0 = 134215681u;  // CRT primes: = 1 mod 2048, 32 q < 2^32
+constexpr uint32_t kQ1 = 134203393u;
 
 
 // Twiddles.  Forward zeta[k] = psi^bitrev10(k) (k = 1..1023), psi a primitive
 // 2048-th root of unity mod q; the stage with m blocks uses zeta[m + block].
-// The warp-uniform ones travel in the kernel parameter block (constant bank),
-// the per-lane ones in global memory.
+// Inverse: omega = psi^2, the DIT stage of half-length h uses omega^-(j 512 / h)
+// for the j-th pair of a block, then the output twist psi^-p.  Every entry is
+// (w, floor(w 2^32 / q)).  The warp-uniform ones travel in the kernel parameter
+// block (constant bank), the per-lane ones in global memory.
 struct TwiddleConst {
-  uint2 fwd1[2][32];  // pass-1 forward zetas, index 1..31, (w, floor(w 2^32 / q))
-  uint2 inv2[2][32];  // pass-2 inverse zetas, index 1..31
+  uint2 fwd1[2][32];      // forward pass 1: zeta[1..31]
+  uint2 inv1[2][32];      // inverse pass 1: index (h - 1) + j, h = 1, 2, 4, 8, 16, j < h
+  uint32_t dig_c[2];      // (-64 - 64 zeta[1]) mod q: first-stage offset for raw digits
+  uint32_t dig_d[2];      // (64 zeta[1] - 64) mod q
 };
 
 struct TwiddleGlobal {
-  uint2 fwd2[2][31 * 32];  // per-lane pass-2 forward zetas [k][lane]
-  uint2 inv1[2][31 * 32];  // per-lane pass-1 inverse zetas [k][lane]
+  uint2 fwd2[2][31 * 32];   // forward pass 2, per lane: [(2^s - 1) + block][lane]
+  uint2 inv2[2][31 * 32];   // inverse pass 2, per lane: [(h/32 - 1) + j mod (h/32)][lane]
+  uint2 twist[2][32 * 32];  // inverse output twist psi^-p, p = lane + 32 e: [e][lane]
 };
-
-
 
 enum : uint32_t {
   kGateAnd = 0, kGateNand, kGateOr, kGateNor, kGateXor, kGateXnor,

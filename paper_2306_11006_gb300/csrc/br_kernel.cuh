@@ -34,9 +34,9 @@ constexpr uint32_t pow_mod(uint64_t b, uint64_t e, uint64_t m) {
 constexpr uint32_t kQ0InvQ1 = pow_mod(kQ0, kQ1 - 2, kQ1);
 constexpr uint32_t kQ0InvQ1Shoup = (uint32_t)(((uint64_t)kQ0InvQ1 << 32) / kQ1);
 constexpr uint64_t kM = (uint64_t)kQ0 * kQ1;
-static_assert(kQ0InvQ1 == 39018686u, "CRT constant");
-static_assert(22ull * kQ0 < (1ull << 32) && 22ull * kQ1 < (1ull << 32), "lazy forward bound");
-static_assert(6ull * 1024 * 64 * (1ull << 31) * 2 < kM, "CRT range must hold the exact products");
+static_assert(32ull * kQ0 < (1ull << 32) && 32ull * kQ1 < (1ull << 32), "lazy transform bounds");
+static_assert(kQ0 > kQ1 && kQ0 < 2ull * kQ1, "CRT difference stays positive");
+static_assert(6ull * 1024 * 64 * (1ull << 31) * 2 < kM / 4, "CRT range must hold the exact products");
 
 // Gadget decomposition offset: 2^10 rounds to the top 21 bits, 64 * 2^(32-7p)
 // recentres each 7-bit digit into [-64, 64).
@@ -102,20 +102,14 @@ __device__ __forceinline__ void named_bar(int id, int threads) {
 
 __device__ __forceinline__ uint32_t modswitch(uint32_t x) { return (x + (1u << 20)) >> 21; }
 
-// (x0 mod q0, x1 mod q1), both fully reduced -> centred integer mod 2^32.
+// (x0 mod q0, x1 mod q1), both fully reduced -> the centred integer, mod 2^32.
+// Garner: X = x0 + q0 k, k = (x1 - x0) q0^-1 mod q1.  The exact value is below
+// 2^50 in magnitude, so it is negative exactly when k >= q1 / 2.
 __device__ __forceinline__ uint32_t crt_torus(uint32_t x0, uint32_t x1) {
-  uint32_t d = x1 + 2u * kQ1 - x0;
-  uint32_t k = csub(shoup_mul<1>(kQ0InvQ1, kQ0InvQ1Shoup, d), kQ1);
-  uint64_t X = (uint64_t)kQ0 * k + x0;
-  uint32_t r = (uint32_t)X;
-  return X > kM / 2 ? r - (uint32_t)kM : r;
-}
-
-template <int P>
-__device__ __forceinline__ uint32_t red12(uint32_t x) {  // [0, 12q) -> [0, 2q)
-  x = csub(x, 8u * Prime<P>::q);
-  x = csub(x, 4u * Prime<P>::q);
-  return csub(x, 2u * Prime<P>::q);
+  const uint32_t d = x1 + 2u * kQ1 - x0;
+  const uint32_t k = csub(shoup_mul(kQ0InvQ1, kQ0InvQ1Shoup, d, kQ1), kQ1);
+  const uint32_t r = kQ0 * k + x0;
+  return k >= kQ1 / 2 ? r - (uint32_t)kM : r;
 }
 
 // Gadget digits of temp = X^a ACC - ACC for both polynomials, computed by the
@@ -131,7 +125,7 @@ __device__ __forceinline__ void make_digits(uint32_t *dig, const uint32_t *A, ui
     uint32_t v = P[j & 1023u];
     v = (j & 1024u) ? 0u - v : v;
     const uint32_t y = v - P[k] + kDecOffset;
-    dig[idx] = (y >> 25) | (((y >> 18) & 0x7Fu) << 8) | (((y >> 11) & 0x7Fu) << 16);
+    dig[idx] = (y >> 25) | ((y >> 10) & 0x7F00u) | ((y << 5) & 0x7F0000u);
   }
 }
 
@@ -183,24 +177,31 @@ __device__ __forceinline__ BrShared br_carve(uint8_t *smem) {
   return s;
 }
 
-// One consumer warp (prime P, row group h) over all tiles of the launch.
-template <int P, int H, int GT>
-__device__ __forceinline__ void br_consumer(const BrShared &S, const BrArgs &args, int g, int h, int lane) {
+// One consumer warp (prime P, row group h) over all tiles of the launch.  The
+// same code serves both primes; the owner of output c (warp (P, c) for H > 1,
+// both outputs for H = 1) keeps that output's accumulator in acc0.
+template <int H, int GT>
+__device__ __forceinline__ void br_consumer(const BrShared &S, const BrArgs &args, int g, int h, int P, int lane) {
   constexpr int kRpg = 6 / H;
   constexpr int kScr = scratch_words<H>();
   constexpr int kGateThreads = 64 * H;
+  constexpr int kStages = br_stages<H, GT>();
   const int n = args.n;
   const int bar_id = 1 + g;
   const int role = h * 2 + P;
   const int wbase = g * 2 * H;  // first warp of this gate
   const int tid_g = role * 32 + lane;
+  const int cA = h < 2 ? h : 0;  // output held in acc0
   uint32_t *A = S.acc + g * 2 * kN;
   uint32_t *D = S.dig + g * 2 * kN;
   uint16_t *abar = S.abar + g * kAbarPitch;
   uint32_t *myscr = S.scratch + (wbase + role) * kScr;
-  const uint2 *tw2 = args.tg->fwd2[P];
-  const uint2 *tw1 = args.tg->inv1[P];
-  constexpr int kStages = br_stages<H, GT>();
+  const PrimeRT pr = prime_rt(P, args.tc);
+  const uint2 *tw1f = args.tc.fwd1[P];
+  const uint2 *tw1i = args.tc.inv1[P];
+  const uint2 *tw2f = args.tg->fwd2[P];
+  const uint2 *tw2i = args.tg->inv2[P];
+  const uint2 *twist = args.tg->twist[P];
   const int tiles = (args.num_jobs + GT - 1) / GT;
   uint32_t it = 0;
 
@@ -234,112 +235,98 @@ __device__ __forceinline__ void br_consumer(const BrShared &S, const BrArgs &arg
         const int r = h * kRpg + rr;
         const int c = r / 3, p = r - 3 * (r / 3);
         const uint32_t *dc = D + c * kN;
+        const uint32_t sel = 0x4440u | (uint32_t)p;  // byte p of the packed digits, zero-extended
         uint32_t x[32];
-        const int sh = 8 * p;
 #pragma unroll
-        for (int e = 0; e < 32; ++e) x[e] = ((dc[lane + 32 * e] >> sh) & 0x7Fu) + (Prime<P>::q - 64u);
-        ntt_fwd<P>(x, myscr, args.tc, tw2, lane);
+        for (int e = 0; e < 32; ++e) x[e] = __byte_perm(dc[lane + 32 * e], 0u, sel);
+        ntt_fwd<true>(x, myscr, tw1f, tw2f, pr, lane);
         // MAC with the NTT-domain key row staged in the ring.
         const uint32_t jc = (it * (uint32_t)n + (uint32_t)i) * 6u + (uint32_t)r;
         const uint32_t slot = jc % kStages;
         mbar_wait(S.full + slot, (jc / kStages) & 1u, S.abort_flag, args.status);
-        const uint4 *B0 = reinterpret_cast<const uint4 *>(S.ring + slot * kChunkWords + (0 * 2 + P) * kN);
-        const uint4 *B1 = reinterpret_cast<const uint4 *>(S.ring + slot * kChunkWords + (1 * 2 + P) * kN);
+        const uint4 *B0 = reinterpret_cast<const uint4 *>(S.ring + slot * kChunkWords + (cA * 2 + P) * kN);
+        const uint4 *B1 = reinterpret_cast<const uint4 *>(S.ring + slot * kChunkWords + ((1 - cA) * 2 + P) * kN);
 #pragma unroll
         for (int e4 = 0; e4 < 8; ++e4) {
           const uint4 b0 = B0[e4 * 32 + lane];
           const uint4 b1 = B1[e4 * 32 + lane];
-          acc0[4 * e4 + 0] += mont_mul<P>(x[4 * e4 + 0], b0.x);
-          acc0[4 * e4 + 1] += mont_mul<P>(x[4 * e4 + 1], b0.y);
-          acc0[4 * e4 + 2] += mont_mul<P>(x[4 * e4 + 2], b0.z);
-          acc0[4 * e4 + 3] += mont_mul<P>(x[4 * e4 + 3], b0.w);
-          acc1[4 * e4 + 0] += mont_mul<P>(x[4 * e4 + 0], b1.x);
-          acc1[4 * e4 + 1] += mont_mul<P>(x[4 * e4 + 1], b1.y);
-          acc1[4 * e4 + 2] += mont_mul<P>(x[4 * e4 + 2], b1.z);
-          acc1[4 * e4 + 3] += mont_mul<P>(x[4 * e4 + 3], b1.w);
+          acc0[4 * e4 + 0] += mont_mul(x[4 * e4 + 0], b0.x, pr);
+          acc0[4 * e4 + 1] += mont_mul(x[4 * e4 + 1], b0.y, pr);
+          acc0[4 * e4 + 2] += mont_mul(x[4 * e4 + 2], b0.z, pr);
+          acc0[4 * e4 + 3] += mont_mul(x[4 * e4 + 3], b0.w, pr);
+          acc1[4 * e4 + 0] += mont_mul(x[4 * e4 + 0], b1.x, pr);
+          acc1[4 * e4 + 1] += mont_mul(x[4 * e4 + 1], b1.y, pr);
+          acc1[4 * e4 + 2] += mont_mul(x[4 * e4 + 2], b1.z, pr);
+          acc1[4 * e4 + 3] += mont_mul(x[4 * e4 + 3], b1.w, pr);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(S.empty + slot);
       }
 
-      const int mb = 16 * P, ob = 16 * (1 - P);
+      // prime P combines coefficients e in [16 P, 16 P + 16) and sends the other half;
+      // register arrays need static indices, hence the selects on P
       if constexpr (H == 1) {
+        // both outputs: one inverse code path, the accumulators swapped between uses
+#pragma unroll 1
+        for (int c = 0; c < 2; ++c) {
+          ntt_inv(acc0, myscr, tw1i, tw2i, twist, pr, lane);
 #pragma unroll
-        for (int e = 0; e < 32; ++e) {
-          acc0[e] = red12<P>(acc0[e]);
-          acc1[e] = red12<P>(acc1[e]);
+          for (int e = 0; e < 32; ++e) {
+            const uint32_t t = acc0[e];
+            acc0[e] = acc1[e];
+            acc1[e] = t;
+          }
         }
-        ntt_inv<P>(acc0, myscr, args.tc, tw1, lane);
-        ntt_inv<P>(acc1, myscr, args.tc, tw1, lane);
         __syncwarp();
 #pragma unroll
         for (int e = 0; e < 16; ++e) {
-          myscr[e * 32 + lane] = csub(acc0[ob + e], Prime<P>::q);
-          myscr[512 + e * 32 + lane] = csub(acc1[ob + e], Prime<P>::q);
+          myscr[e * 32 + lane] = P ? acc0[e] : acc0[16 + e];
+          myscr[512 + e * 32 + lane] = P ? acc1[e] : acc1[16 + e];
         }
         named_bar(bar_id, kGateThreads);  // B2: CRT halves posted
         const uint32_t *peer = S.scratch + (wbase + (1 - P)) * kScr;
 #pragma unroll
         for (int e = 0; e < 16; ++e) {
-          const uint32_t m0 = csub(acc0[mb + e], Prime<P>::q), m1 = csub(acc1[mb + e], Prime<P>::q);
+          const uint32_t m0 = P ? acc0[16 + e] : acc0[e], m1 = P ? acc1[16 + e] : acc1[e];
           const uint32_t o0 = peer[e * 32 + lane], o1 = peer[512 + e * 32 + lane];
-          const uint32_t r0 = P == 0 ? crt_torus(m0, o0) : crt_torus(o0, m0);
-          const uint32_t r1 = P == 0 ? crt_torus(m1, o1) : crt_torus(o1, m1);
-          A[lane + 32 * (mb + e)] += r0;
-          A[kN + lane + 32 * (mb + e)] += r1;
+          const int pos = lane + 32 * (16 * P + e);
+          A[pos] += P == 0 ? crt_torus(m0, o0) : crt_torus(o0, m0);
+          A[kN + pos] += P == 0 ? crt_torus(m1, o1) : crt_torus(o1, m1);
         }
         named_bar(bar_id, kGateThreads);  // B3: ACC updated
       } else {
-        // reduce partial sums over the H row groups into the owner warp (P, c)
-        if (h != 0) {
-          __syncwarp();
+        // partial sums meet in the owner warp (P, c) of each output c: half c of a
+        // warp's scratch holds its partial of output c (the owner's own half c
+        // stays free for its inverse transform and CRT exchange)
+        __syncwarp();
+        if (h >= 2) {
 #pragma unroll
-          for (int e = 0; e < 32; ++e) myscr[e * 32 + lane] = acc0[e];
+          for (int e = 0; e < 32; ++e) myscr[cA * kXpose + e * 32 + lane] = acc0[e];
         }
-        if (h != 1) {
-          __syncwarp();
 #pragma unroll
-          for (int e = 0; e < 32; ++e) myscr[kXpose + e * 32 + lane] = acc1[e];
-        }
+        for (int e = 0; e < 32; ++e) myscr[(1 - cA) * kXpose + e * 32 + lane] = acc1[e];
         named_bar(bar_id, kGateThreads);  // B1: partials posted
         if (h < 2) {
           uint32_t *half = myscr + h * kXpose;
-          if (h == 0) {
-            for (int hp = 1; hp < H; ++hp) {
-              const uint32_t *src = S.scratch + (wbase + hp * 2 + P) * kScr;
+          for (int hp = 0; hp < H; ++hp) {
+            if (hp == h) continue;
+            const uint32_t *src = S.scratch + (wbase + hp * 2 + P) * kScr + h * kXpose;
 #pragma unroll
-              for (int e = 0; e < 32; ++e) acc0[e] += src[e * 32 + lane];
-            }
-#pragma unroll
-            for (int e = 0; e < 32; ++e) acc0[e] = red12<P>(acc0[e]);
-            ntt_inv<P>(acc0, half, args.tc, tw1, lane);
-            __syncwarp();
-#pragma unroll
-            for (int e = 0; e < 16; ++e) half[e * 32 + lane] = csub(acc0[ob + e], Prime<P>::q);
-          } else {
-            for (int hp = 0; hp < H; ++hp) {
-              if (hp == 1) continue;
-              const uint32_t *src = S.scratch + (wbase + hp * 2 + P) * kScr + kXpose;
-#pragma unroll
-              for (int e = 0; e < 32; ++e) acc1[e] += src[e * 32 + lane];
-            }
-#pragma unroll
-            for (int e = 0; e < 32; ++e) acc1[e] = red12<P>(acc1[e]);
-            ntt_inv<P>(acc1, half, args.tc, tw1, lane);
-            __syncwarp();
-#pragma unroll
-            for (int e = 0; e < 16; ++e) half[e * 32 + lane] = csub(acc1[ob + e], Prime<P>::q);
+            for (int e = 0; e < 32; ++e) acc0[e] += src[e * 32 + lane];
           }
+          ntt_inv(acc0, half, tw1i, tw2i, twist, pr, lane);
+          __syncwarp();
+#pragma unroll
+          for (int e = 0; e < 16; ++e) half[e * 32 + lane] = P ? acc0[e] : acc0[16 + e];
         }
         named_bar(bar_id, kGateThreads);  // B2: CRT halves posted
         if (h < 2) {
-          const int c = h;
-          const uint32_t *peer = S.scratch + (wbase + c * 2 + (1 - P)) * kScr + c * kXpose;
+          const uint32_t *peer = S.scratch + (wbase + h * 2 + (1 - P)) * kScr + h * kXpose;
 #pragma unroll
           for (int e = 0; e < 16; ++e) {
-            const uint32_t m = csub(c == 0 ? acc0[mb + e] : acc1[mb + e], Prime<P>::q);
+            const uint32_t m = P ? acc0[16 + e] : acc0[e];
             const uint32_t o = peer[e * 32 + lane];
-            A[c * kN + lane + 32 * (mb + e)] += P == 0 ? crt_torus(m, o) : crt_torus(o, m);
+            A[h * kN + lane + 32 * (16 * P + e)] += P == 0 ? crt_torus(m, o) : crt_torus(o, m);
           }
         }
         named_bar(bar_id, kGateThreads);  // B3: ACC updated
@@ -405,11 +392,7 @@ __global__ void __launch_bounds__((2 * H * GT + 1) * 32, 1) br_kernel(const __gr
     return;
   }
   const int g = warp / (2 * H), role = warp % (2 * H);
-  const int P = role & 1, h = role >> 1;
-  if (P == 0)
-    br_consumer<0, H, GT>(S, args, g, h, lane);
-  else
-    br_consumer<1, H, GT>(S, args, g, h, lane);
+  br_consumer<H, GT>(S, args, g, role >> 1, role & 1, lane);
 }
 
 template <int H, int GT>

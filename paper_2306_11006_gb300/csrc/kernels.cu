@@ -31,29 +31,29 @@ namespace {
 // transform's 1/N and the Montgomery factor of the MAC), fully reduced, and
 // stored in the per-lane order the MAC reads: [e/4][lane][e%4].
 // ---------------------------------------------------------------------------
-template <int P>
 __device__ void bsk_poly_to_ntt(const uint32_t *src, uint32_t *dst, uint32_t *xbuf, const TwiddleConst &tc,
-                                const TwiddleGlobal *tg, int lane) {
-  constexpr uint32_t q = Prime<P>::q;
+                                const TwiddleGlobal *tg, int P, int lane) {
+  const PrimeRT pr = prime_rt(P, tc);
+  const uint32_t q = pr.q;
   constexpr uint32_t kScale = 1u << 22;  // N^-1 2^32 mod q = 2^22
   uint32_t x[32];
 #pragma unroll
   for (int e = 0; e < 32; ++e) {
-    int32_t v = (int32_t)src[lane + 32 * e];
-    int32_t m = v % (int32_t)q;
+    const int32_t v = (int32_t)src[lane + 32 * e];
+    const int32_t m = v % (int32_t)q;
     x[e] = (uint32_t)(m < 0 ? m + (int32_t)q : m);
   }
-  ntt_fwd<P>(x, xbuf, tc, tg->fwd2[P], lane);
+  ntt_fwd<false>(x, xbuf, tc.fwd1[P], tg->fwd2[P], pr, lane);
 #pragma unroll
   for (int e = 0; e < 32; ++e) {
-    uint32_t v = x[e] % q;
+    const uint32_t v = x[e] % q;
     dst[(e >> 2) * 128 + lane * 4 + (e & 3)] = (uint32_t)((uint64_t)v * kScale % q);
   }
 }
 
 __global__ void bsk_to_ntt_kernel(const uint32_t *__restrict__ bsk, int n, uint32_t *__restrict__ out,
                                   const __grid_constant__ TwiddleConst tc, const TwiddleGlobal *tg) {
-  __shared__ uint32_t xbuf[4][kXpose];
+  __shared__ __align__(16) uint32_t xbuf[4][kXpose];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long wid = (long long)blockIdx.x * 4 + warp;
   const long long total = (long long)n * 12 * 2;
@@ -64,10 +64,7 @@ __global__ void bsk_to_ntt_kernel(const uint32_t *__restrict__ bsk, int n, uint3
   const int c = (int)(poly & 1);
   const uint32_t *src = bsk + poly * kN;
   uint32_t *dst = out + ir * kChunkWords + (size_t)(c * 2 + P) * kN;
-  if (P == 0)
-    bsk_poly_to_ntt<0>(src, dst, xbuf[warp], tc, tg, lane);
-  else
-    bsk_poly_to_ntt<1>(src, dst, xbuf[warp], tc, tg, lane);
+  bsk_poly_to_ntt(src, dst, xbuf[warp], tc, tg, P, lane);
 }
 
 // ---------------------------------------------------------------------------

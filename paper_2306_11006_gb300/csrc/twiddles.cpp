@@ -1,8 +1,10 @@
 // twiddles.cpp -- twiddle tables of the device NTTs for the CRT primes q0, q1.
 //
-// zeta[k] = psi^bitrev10(k) for k = 1..1023, psi a primitive 2048-th root of
-// unity mod q (psi^1024 = -1), so the negacyclic Cooley-Tukey stage with m blocks
-// uses zeta[m + block]; the inverse uses zeta^-1 at the same positions.  Each
+// Forward (negacyclic, merged twist): zeta[k] = psi^bitrev10(k) for k = 1..1023,
+// psi a primitive 2048-th root of unity mod q (psi^1024 = -1); the stage with m
+// blocks uses zeta[m + block].  Inverse (cyclic DIT on the bit-reversed
+// spectrum, omega = psi^2): the stage of half-length h uses omega^-(j 512 / h) for
+// the j-th pair of each block, followed by the twist psi^-p at output p.  Every
 // entry carries its Shoup companion floor(w 2^32 / q).
 #include <cstdint>
 #include <stdexcept>
@@ -46,28 +48,37 @@ void fill(int P, uint64_t q, TwiddleConst *tc, TwiddleGlobal *tg) {
     }
   }
   if (!psi) throw std::runtime_error("no 2048-th root of unity");
-  uint64_t zeta[1024], zinv[1024];
-  for (uint32_t k = 1; k < 1024; ++k) {
-    zeta[k] = pw(psi, bitrev10(k), q);
-    zinv[k] = pw(zeta[k], q - 2, q);
+  const uint64_t psi_inv = pw(psi, q - 2, q);
+  const uint64_t omega_inv = psi_inv * psi_inv % q;
+  uint64_t zeta[1024];
+  for (uint32_t k = 1; k < 1024; ++k) zeta[k] = pw(psi, bitrev10(k), q);
+  zeta[0] = 1;
+  for (int zi = 0; zi < 32; ++zi) tc->fwd1[P][zi] = entry(zeta[zi], q);
+  tc->dig_c[P] = (uint32_t)((2 * q - 64 - 64 * zeta[1] % q) % q);
+  tc->dig_d[P] = (uint32_t)((64 * zeta[1] % q + q - 64) % q);
+  // forward pass 2, per lane: stage s (length 16 >> s) has 2^s blocks per lane;
+  // block b of lane l is zeta index 2^s (32 + l) + b, stored at [(2^s - 1 + b)][l].
+  for (int s = 0; s < 5; ++s)
+    for (int b = 0; b < (1 << s); ++b)
+      for (int lane = 0; lane < 32; ++lane)
+        tg->fwd2[P][((1 << s) - 1 + b) * 32 + lane] = entry(zeta[(1 << s) * (32 + lane) + b], q);
+  // inverse pass 1 (half-lengths 1..16 within a lane): omega^-(j 512 / h)
+  for (int zi = 0; zi < 32; ++zi) tc->inv1[P][zi] = entry(1, q);
+  for (int t = 0; t < 5; ++t) {
+    const int h = 1 << t;
+    for (int j = 0; j < h; ++j) tc->inv1[P][(h - 1) + j] = entry(pw(omega_inv, (uint64_t)j * (512 / h), q), q);
   }
-  zeta[0] = zinv[0] = 1;
-  for (int zi = 0; zi < 32; ++zi) {
-    tc->fwd1[P][zi] = entry(zeta[zi], q);
-    tc->inv2[P][zi] = entry(zinv[zi], q);
-  }
-  // per-lane tables: stage s (length 16 >> s) has 2^s blocks per lane; block b of
-  // lane l is zeta index 2^s (32 + l) + b, stored at [(2^s - 1 + b)][l].
+  // inverse pass 2 (half-lengths 32..512 across e): pair index j = lane + 32 b,
+  // b < h / 32, twiddle omega^-(j 512 / h), stored at [(h/32 - 1) + b][lane]
   for (int s = 0; s < 5; ++s) {
-    for (int b = 0; b < (1 << s); ++b) {
-      for (int lane = 0; lane < 32; ++lane) {
-        const int zi = (1 << s) * (32 + lane) + b;
-        const int k = (1 << s) - 1 + b;
-        tg->fwd2[P][k * 32 + lane] = entry(zeta[zi], q);
-        tg->inv1[P][k * 32 + lane] = entry(zinv[zi], q);
-      }
-    }
+    const int hr = 1 << s, h = 32 * hr;
+    for (int b = 0; b < hr; ++b)
+      for (int lane = 0; lane < 32; ++lane)
+        tg->inv2[P][(hr - 1 + b) * 32 + lane] = entry(pw(omega_inv, (uint64_t)(lane + 32 * b) * (512 / h), q), q);
   }
+  // output twist psi^-p at p = lane + 32 e
+  for (int e = 0; e < 32; ++e)
+    for (int lane = 0; lane < 32; ++lane) tg->twist[P][e * 32 + lane] = entry(pw(psi_inv, lane + 32 * e, q), q);
 }
 
 }  // namespace
