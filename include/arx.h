@@ -166,9 +166,10 @@ int arx_plan_profile(int plan, const uint32_t *ct_in, float *br_ms, float *ks_ms
                      uint32_t *ks_launches);
 
 /* Force the blind-rotation launch shape: 2H warps per gate (H in 1, 2, 3, 6)
- * and GT gates per CTA; (0, 0) restores the automatic choice.  Shapes:
- * (6,1) (3,1) (3,2) (2,1) (2,3) (1,1) (1,2) (1,4) (1,6).  Plans keep the shapes
- * chosen when they were created. */
+ * and GT gates per CTA, or (12, 1): one gate on a cluster of two CTAs (two SMs,
+ * 12 warps); (0, 0) restores the automatic choice.  Shapes: (12,1) (6,1) (3,1)
+ * (3,2) (2,1) (2,3) (1,1) (1,2) (1,4) (1,6).  Plans keep the shapes chosen when
+ * they were created. */
 int arx_set_launch_shape(int H, int GT);
 
 /* ------------------------------------------------------------ serving ---- */

@@ -103,6 +103,13 @@ int ks_splits(int num_jobs, int sms);
 cudaError_t launch_gather(const uint32_t *wires, const uint32_t *idx, int count, int n, uint32_t *dst,
                           int dst_stride, cudaStream_t st);
 
+// Cluster shape {kClusterH, 1}: one gate on a cluster of two CTAs (two SMs);
+// its grid is counted in clusters.
+constexpr int kClusterH = 12;
+size_t br_cluster_smem();
+cudaError_t launch_br_cluster(const BrArgs &args, int clusters, cudaStream_t st);
+int br_cluster_occupancy();  // co-resident clusters on the device (0: cannot launch)
+
 // per-shape launchers (one translation unit per H)
 cudaError_t launch_br_h1(const BrArgs &args, int GT, int grid, cudaStream_t st);
 cudaError_t launch_br_h2(const BrArgs &args, int GT, int grid, cudaStream_t st);

@@ -15,7 +15,7 @@ from paper_2306_11006_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
 
-SHAPES = [(6, 1), (3, 1), (3, 2), (2, 1), (2, 3), (1, 1), (1, 2), (1, 4), (1, 6)]
+SHAPES = [(12, 1), (6, 1), (3, 1), (3, 2), (2, 1), (2, 3), (1, 1), (1, 2), (1, 4), (1, 6)]
 
 
 @pytest.fixture(scope="session")
