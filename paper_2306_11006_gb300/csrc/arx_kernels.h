@@ -29,12 +29,18 @@ struct TwiddleConst {
   uint2 inv1[2][32];      // inverse pass 1: index (h - 1) + j, h = 1, 2, 4, 8, 16, j < h
   uint32_t dig_c[2];      // (-64 - 64 zeta[1]) mod q: first-stage offset for raw digits
   uint32_t dig_d[2];      // (64 zeta[1] - 64) mod q
+  uint2 psi512[2];        // psi^-512 and psi^-256 (last stages of the split inverse)
+  uint2 psi256[2];
 };
 
 struct TwiddleGlobal {
   uint2 fwd2[2][31 * 32];   // forward pass 2, per lane: [(2^s - 1) + block][lane]
   uint2 inv2[2][31 * 32];   // inverse pass 2, per lane: [(h/32 - 1) + j mod (h/32)][lane]
   uint2 twist[2][32 * 32];  // inverse output twist psi^-p, p = lane + 32 e: [e][lane]
+  // split transforms of the cluster kernel
+  uint2 fwdh[2][2][15 * 32];  // forward pass 2 of half w: [prime][w][(2^s - 1) + block][lane]
+  uint4 fin[2][512];          // split inverse, last two stages + twist, k < 256:
+                              // [2k] = {psi^-k, psi^-5k}, [2k+1] = {psi^-3k, psi^-7k}, with companions
 };
 
 enum : uint32_t {

@@ -4,18 +4,24 @@
 // The paper runs one gate per SM and names spreading a gate over several SMs as
 // the remedy for thin waves (Sec. 8).  Here the two TLWE components split the
 // work: CTA h of the cluster owns accumulator polynomial ACC_h and the three TGSW
-// rows whose digits come from ACC_h (rows 3h .. 3h+2), for both CRT primes (six
-// consumer warps, one forward transform each per CMux).  Each warp writes its
-// row's key products for both outputs to local shared memory; after a barrier
-// of the three warps of its prime, each of them adds the three rows of output
-// 1-h over one third of the coefficients and stores that third into the peer's
-// shared memory (distributed shared memory, 8 KiB per CMux and CTA).  So CTA h
-// ends each CMux holding the complete sums of output h in both primes: it runs
-// the inverse transforms, the CRT and the update of ACC_h by itself, and never
-// needs ACC_{1-h}.  The only cross-SM dependency per CMux is one mbarrier in
-// each CTA that the peer's warps arrive on remotely (one release at cluster
-// scope per warp) after their stores; the two owner warps wait on it with a
-// bounded wait, and all six warps then share the CRT.
+// rows whose digits come from ACC_h (rows 3h .. 3h+2), for both CRT primes.  Each
+// forward 1024-point transform is split over two warps (halves w = 0, 1): its
+// first stage (distance 512) is taken while loading the digits, after which the
+// halves are independent 512-point transforms.  Each inverse transform is split
+// over four warps (quarters of the spectrum), whose last two stages and the
+// output twist are folded into the CRT pass that all warps share.  So twelve
+// consumer warps per CTA: (row, prime, half); eight of them run the inverses.
+//
+// Each warp writes its key products for both outputs to local shared memory;
+// after a barrier of the six warps of its prime, each adds the three rows of
+// output 1-h over a sixth of the coefficients into a staging buffer and has the
+// bulk copy engine move it into the peer's shared memory (distributed shared
+// memory, 8 KiB per CMux and CTA), completing its bytes on the peer's mbarrier.
+// So CTA h ends each CMux holding the complete sums of output h in both primes:
+// it runs the inverse transforms, the CRT and the update of ACC_h by itself, and
+// never needs ACC_{1-h}.  The only cross-SM dependency per CMux is that
+// transaction count (one mbarrier per CMux parity in each CTA); no thread fences
+// at cluster scope, and the owner warps wait with a bounded wait.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -25,12 +31,12 @@
 namespace arx {
 namespace brc {
 
-constexpr int kCons = 6;                      // consumer warps: (row 0..2) x (prime 0..1)
+constexpr int kCons = 12;                     // consumer warps: (row 0..2) x (prime 0..1) x (half 0..1)
 constexpr int kThreads = (kCons + 1) * 32;    // + producer warp
-constexpr int kStages = 6;                    // ring of 16 KiB key rows: two CMux ahead
+constexpr int kStages = 4;                    // ring of 16 KiB key rows (smaller ring, larger L1 for twiddles)
 constexpr int kAbarPitch = 640;
 constexpr long long kWaitCycles = 4000000000ll;
-constexpr uint32_t kArrivals = kCons;        // the peer's consumer warps, per CMux
+constexpr uint32_t kPeerBytes = 2 * kN * 4;  // the peer's row sums (both primes) per CMux
 constexpr uint32_t kDecOffset = (1u << 10) + (64u << 25) + (64u << 18) + (64u << 11);
 
 constexpr uint32_t pow_mod(uint64_t b, uint64_t e, uint64_t m) {
@@ -50,14 +56,16 @@ constexpr uint64_t kM = (uint64_t)kQ0 * kQ1;
 // shared memory (bytes)
 constexpr size_t kRingBytes = (size_t)kStages * kChunkBytes;
 constexpr size_t kAccBytes = kN * 4;                // ACC_h
-constexpr size_t kDigBytes = kN * 4;                // packed digits of ACC_h
+constexpr size_t kDigBytes = 3 * 256 * 4;           // digits of ACC_h: [row][k] bytes of k, k+256, k+512, k+768
 constexpr size_t kSumBytes = 2 * 2 * 3 * kN * 4;    // [output own/other][prime 2][row 3][N] products
 constexpr size_t kSlotBytes = 2 * 2 * kN * 4;       // [parity 2][prime 2][N] the peer's row sums
-constexpr size_t kScrBytes = (size_t)kCons * kXpose * 4;
+constexpr size_t kStageBytes = 2 * 2 * kN * 4;      // [parity 2][prime 2][N] row sums sent to the peer
+constexpr int kHalf = 512;                    // words per half transform
+constexpr size_t kScrBytes = (size_t)kCons * kHalf * 4;
 constexpr size_t kAbarBytes = kAbarPitch * 2;
-constexpr size_t kBarBytes = (2 * kStages + 1) * 8 + 16;
+constexpr size_t kBarBytes = (2 * kStages + 2) * 8 + 16;
 constexpr size_t kSmem =
-    kRingBytes + kAccBytes + kDigBytes + kSumBytes + kSlotBytes + kScrBytes + kAbarBytes + kBarBytes;
+    kRingBytes + kAccBytes + kDigBytes + kSumBytes + kSlotBytes + kStageBytes + kScrBytes + kAbarBytes + kBarBytes;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -77,16 +85,22 @@ __device__ __forceinline__ void cluster_sync_all() {
   asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
-__device__ __forceinline__ void st_remote_v4(uint32_t caddr, uint4 v) {
-  asm volatile("st.shared::cluster.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(caddr), "r"(v.x), "r"(v.y), "r"(v.z),
-               "r"(v.w)
-               : "memory");
+// Bulk copy from this CTA's shared memory into a peer CTA's shared memory; the
+// bytes complete on the peer's mbarrier.  Both addresses 16-byte aligned, size a
+// multiple of 16.
+__device__ __forceinline__ void bulk_s2peer(uint32_t dst_cluster, const void *src, uint32_t bytes,
+                                            uint32_t bar_cluster) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          dst_cluster),
+      "r"(smem_u32(src)), "r"(bytes), "r"(bar_cluster)
+      : "memory");
 }
 
-// Arrive on an mbarrier of any CTA of the cluster, releasing this thread's prior
-// writes (and those ordered before them) at cluster scope.
-__device__ __forceinline__ void mbar_arrive_cluster(uint32_t caddr) {
-  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(caddr) : "memory");
+// Orders this thread's generic-proxy writes to shared memory before later
+// async-proxy (bulk copy) reads of them.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
@@ -113,24 +127,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
   return ok != 0;
 }
 
-__device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t *bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-template <bool kCluster>
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
                                           unsigned int *status) {
   if (*abort_flag) return false;
-  auto probe = [&] { return kCluster ? mbar_try_wait_cluster(bar, parity) : mbar_try_wait(bar, parity); };
-  if (probe()) return true;
+  if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
-  while (!probe()) {
+  while (!mbar_try_wait(bar, parity)) {
     if (*abort_flag) return false;
     if (clock64() - t0 > kWaitCycles) {
       *abort_flag = 1;
@@ -162,20 +164,143 @@ __device__ __forceinline__ uint32_t crt_torus(uint32_t x0, uint32_t x1) {
   return k >= kQ1 / 2 ? r - (uint32_t)kM : r;
 }
 
+// Word offset of position p in a buffer of 32-word rows: the 16-byte chunks of
+// row p >> 5 are XOR-swizzled by the row index (see swz), so that storing 32
+// consecutive positions, and 128-bit loads of 16 (or 8) consecutive positions per
+// lane with the block order below, are free of bank conflicts.
+__device__ __forceinline__ int swp(int p) { return swz(p >> 5, p & 31); }
+
+// Block of 16 positions that lane l holds after the forward transpose.
+__device__ __forceinline__ int fwd_block(int lane) { return 2 * (lane & 15) + (lane >> 4); }
+
+// Butterfly between lanes (partner lane ^ mask): the lower lane holds x, the
+// upper lane y; returns x + z y or x - z y + 2q.
+__device__ __forceinline__ uint32_t xlane_bfly(uint32_t v, uint2 z, bool upper, int mask, const PrimeRT &pr) {
+  const uint32_t o = __shfl_xor_sync(0xffffffffu, v, mask);
+  const uint32_t y = upper ? v : o, x = upper ? o : v;
+  const uint32_t t = shoup_mul(z.x, z.y, y, pr.q);
+  return upper ? x - t + pr.q2 : x + t;
+}
+
+// Forward half transform (negacyclic Cooley-Tukey, merged twist), positions
+// 512 w + p.  In: x[e] = stage-1 output at p = lane + 32 e (< 3q + 128).
+// Out: x[e] = spectral position 512 w + 16 b + e, b = fwd_block(lane) (< 22q),
+// bit-reversed order.
+__device__ __forceinline__ void fwd_half(uint32_t (&x)[16], uint32_t *xbuf, const uint2 *tw1,
+                                         const uint2 *__restrict__ tw2, const uint2 *__restrict__ twh, int w,
+                                         const PrimeRT &pr, int lane) {
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {  // lengths 256, 128, 64, 32: bits 3 .. 0 of e
+    const int lr = 8 >> s, m = 2 << s;
+#pragma unroll
+    for (int e = 0; e < 16; ++e)
+      if ((e & lr) == 0) ct_bfly(x[e], x[e + lr], tw1[m + (m >> 1) * w + e / (2 * lr)], pr);
+  }
+  {  // length 16: lane bit 4, zeta[32 + 16 w + e]
+    const bool up = (lane & 16) != 0;
+#pragma unroll
+    for (int e = 0; e < 16; ++e) x[e] = xlane_bfly(x[e], __ldg(tw2 + 16 * w + e), up, 16, pr);
+  }
+  __syncwarp();
+#pragma unroll
+  for (int e = 0; e < 16; ++e) xbuf[swp(lane + 32 * e)] = x[e];
+  __syncwarp();
+  const uint4 *xb4 = reinterpret_cast<const uint4 *>(xbuf);
+  const int b = fwd_block(lane);
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const uint4 v = xb4[swp(16 * b + 4 * c) >> 2];
+    x[4 * c + 0] = v.x;
+    x[4 * c + 1] = v.y;
+    x[4 * c + 2] = v.z;
+    x[4 * c + 3] = v.w;
+  }
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {  // lengths 8, 4, 2, 1 with per-lane twiddles
+    const int len = 8 >> s, k0 = (1 << s) - 1;
+    uint2 z;
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+      if ((e & len) == 0) {
+        if ((e & (2 * len - 1)) == 0) z = __ldg(twh + (k0 + e / (2 * len)) * 32 + lane);
+        ct_bfly(x[e], x[e + len], z, pr);
+      }
+    }
+  }
+}
+
+// Inverse quarter transform (cyclic Cooley-Tukey DIT with omega^-1) of spectral
+// positions 256 Q .. 256 Q + 255, all stages but the last two (half-lengths
+// 1 .. 128).  In: x[e] = position 256 Q + 8 lane + e (< 12 q).  Out: x[e] =
+// position lane + 32 e of the quarter's natural-order result (< 28 q).
+__device__ __forceinline__ void inv_quarter(uint32_t (&x)[8], uint32_t *xbuf, const uint2 *tw1,
+                                            const uint2 *__restrict__ tw2, const PrimeRT &pr, int lane) {
+#pragma unroll
+  for (int t = 0; t < 3; ++t) {  // half-lengths 1, 2, 4: bits 0 .. 2 of e
+    const int hh = 1 << t;
+#pragma unroll
+    for (int e = 0; e < 8; ++e)
+      if ((e & hh) == 0) ct_bfly(x[e], x[e + hh], tw1[(hh - 1) + (e & (hh - 1))], pr);
+  }
+  {  // half-length 8: lane bit 0, omega^-(64 e)
+    const bool up = (lane & 1) != 0;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) x[e] = xlane_bfly(x[e], tw1[7 + e], up, 1, pr);
+  }
+  {  // half-length 16: lane bit 1, omega^-(32 (8 (lane & 1) + e))
+    const bool up = (lane & 2) != 0, odd = (lane & 1) != 0;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const uint2 za = tw1[15 + e], zb = tw1[23 + e];
+      x[e] = xlane_bfly(x[e], odd ? zb : za, up, 2, pr);
+    }
+  }
+  __syncwarp();
+  uint4 *xb4 = reinterpret_cast<uint4 *>(xbuf);
+#pragma unroll
+  for (int c = 0; c < 2; ++c)
+    xb4[swp(8 * lane + 4 * c) >> 2] = make_uint4(x[4 * c], x[4 * c + 1], x[4 * c + 2], x[4 * c + 3]);
+  __syncwarp();
+#pragma unroll
+  for (int e = 0; e < 8; ++e) x[e] = xbuf[swp(lane + 32 * e)];
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {  // half-lengths 32, 64, 128: bits 0 .. 2 of e
+    const int hr = 1 << s;
+#pragma unroll
+    for (int e = 0; e < 8; ++e)
+      if ((e & hr) == 0) ct_bfly(x[e], x[e + hr], __ldg(tw2 + ((hr - 1) + (e & (hr - 1))) * 32 + lane), pr);
+  }
+}
+
+// Last two inverse stages, output twist and full reduction for one prime:
+// outputs k, k + 256, k + 512, k + 768 from the quarters' outputs u_Q at k.
+__device__ __forceinline__ void inv_last(uint32_t (&o)[4], const uint32_t (&u)[4], uint4 f01, uint4 f23,
+                                         uint2 m512, uint2 m256, uint32_t q) {
+  const uint32_t t0 = shoup_mul(f01.x, f01.y, u[0], q), t1 = shoup_mul(f01.z, f01.w, u[1], q);
+  const uint32_t t2 = shoup_mul(f23.x, f23.y, u[2], q), t3 = shoup_mul(f23.z, f23.w, u[3], q);
+  const uint32_t s01 = t0 + t1, d01 = t0 - t1 + 2u * q, s23 = t2 + t3, d23 = t2 - t3 + 2u * q;  // < 4q
+  o[0] = csub(csub(csub(s01 + s23, 4u * q), 2u * q), q);
+  o[2] = csub(shoup_mul(m512.x, m512.y, s01 - s23 + 4u * q, q), q);
+  const uint32_t e23 = shoup_mul(m512.x, m512.y, d23, q), e01 = shoup_mul(m512.x, m512.y, d01, q);
+  o[1] = csub(shoup_mul(m256.x, m256.y, d01 + e23, q), q);
+  o[3] = csub(shoup_mul(m256.x, m256.y, e01 + d23, q), q);
+}
+
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     br_cluster_kernel(const __grid_constant__ BrArgs args) {
   extern __shared__ __align__(128) uint8_t smem[];
   uint32_t *ring = reinterpret_cast<uint32_t *>(smem);
   uint32_t *A = reinterpret_cast<uint32_t *>(smem + kRingBytes);
-  uint32_t *D = A + kN;
-  uint32_t *sums = D + kN;                          // [output][prime][row][N], 16-byte chunks swizzled
-  uint32_t *slots = sums + 12 * kN;                 // [parity][prime][N], same chunk order
-  uint32_t *scratch = slots + 4 * kN;               // [warp][kXpose]
-  uint16_t *abar = reinterpret_cast<uint16_t *>(scratch + kCons * kXpose);
+  uint32_t *D = A + kN;                             // [row][256]
+  uint32_t *sums = D + 3 * 256;                         // [output own/other][prime][row][N], halves swizzled (swh)
+  uint32_t *slots = sums + 12 * kN;                 // [parity][prime][N], same layout
+  uint32_t *stage = slots + 4 * kN;                 // [parity][prime][N], same layout
+  uint32_t *scratch = stage + 4 * kN;               // [warp][kHalf]; the inverse warps post here
+  uint16_t *abar = reinterpret_cast<uint16_t *>(scratch + kCons * kHalf);
   uint64_t *full = reinterpret_cast<uint64_t *>(abar + kAbarPitch);
   uint64_t *empty = full + kStages;
-  uint64_t *done = empty + kStages;                 // the peer's row sums of a CMux in place
-  volatile int *abort_flag = reinterpret_cast<volatile int *>(done + 1);
+  uint64_t *done = empty + kStages;                 // [parity]: the peer's row sums of a CMux in place
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(done + 2);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t h = cluster_rank();                // accumulator component owned here
@@ -183,9 +308,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(full + s, 1);
-      mbar_init(empty + s, 2);
+      mbar_init(empty + s, 4);  // the four warps (prime, half) of a row
     }
-    mbar_init(done, kArrivals);
+    mbar_init(done + 0, 1);  // one local arrival (with the expected bytes) per CMux
+    mbar_init(done + 1, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -194,6 +320,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
   const int n = args.n;
   const int nclusters = gridDim.x / 2, cid = blockIdx.x / 2;
   const int tiles = args.num_jobs;
+  constexpr int kConsThreads = kCons * 32;
 
   if (warp == kCons) {  // producer: stream this CTA's three key rows of every CMux
     if (lane == 0 && tiles > 0) {
@@ -204,7 +331,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
           for (int rr = 0; rr < 3; ++rr, ++jc) {
             const uint32_t slot = jc % kStages;
             if (jc >= (uint32_t)kStages &&
-                !mbar_wait<false>(empty + slot, ((jc / kStages) - 1) & 1u, abort_flag, args.status)) {
+                !mbar_wait(empty + slot, ((jc / kStages) - 1) & 1u, abort_flag, args.status)) {
               ok = false;
               break;
             }
@@ -223,115 +350,158 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
       }
     }
   } else if (tiles > 0) {
-    const int rr = warp >> 1, P = warp & 1;         // row 3h + rr, prime P
-    const int tid = threadIdx.x;                    // 0 .. 191
+    const int rr = warp >> 2, P = (warp >> 1) & 1, w = warp & 1;  // row 3h + rr, prime P, half w
+    const int tid = threadIdx.x;                                   // 0 .. 383
     const PrimeRT pr = prime_rt(P, args.tc);
-    uint32_t *myscr = scratch + warp * kXpose;
+    uint32_t *myscr = scratch + warp * kHalf;
     const uint2 *tw1f = args.tc.fwd1[P], *tw1i = args.tc.inv1[P];
-    const uint2 *tw2f = args.tg->fwd2[P], *tw2i = args.tg->inv2[P], *twist = args.tg->twist[P];
-    const uint32_t done_remote = map_peer(smem_u32(done), peer);
+    const uint2 *tw2f = args.tg->fwd2[P], *tw2i = args.tg->inv2[P], *twh = args.tg->fwdh[P][w];
+    const uint2 z1 = args.tc.fwd1[P][1];
+    // chunks [c0, c0 + nc) of a prime's row sum are this warp's to send
+    const int c0 = (rr * 2 + w) * 43, nc = c0 + 43 <= 256 ? 43 : 256 - c0;
+    const int fb = fwd_block(lane);
+    // inverse: warps of rows 0, 1 take quarter Q = 2 rr + w of prime P
+    const int Qd = 2 * rr + w;
+    // quarter Q of prime P is posted by warp ((Q >> 1) * 2 + P) * 2 + (Q & 1); prime 1 lies 2 kHalf above prime 0
+    const uint32_t *post0[4];
+#pragma unroll
+    for (int Q = 0; Q < 4; ++Q) post0[Q] = scratch + ((Q >> 1) * 4 + (Q & 1)) * kHalf;
     uint32_t it = 0, cm = 0;  // tile counter, CMux counter
     for (int tile = cid; tile < tiles; tile += nclusters, ++it) {
       const BrJob jb = args.jobs[tile];
       const uint32_t *wa = args.wires + (size_t)jb.ia * kWireStride;
       const uint32_t *wb = args.wires + (size_t)jb.ib * kWireStride;
       const uint32_t sa = (uint32_t)(int32_t)jb.sa, sb = (uint32_t)(int32_t)jb.sb;
-      for (int k = tid; k < n; k += kCons * 32) abar[k] = (uint16_t)modswitch(sa * wa[k] + sb * wb[k]);
+      for (int k = tid; k < n; k += kConsThreads) abar[k] = (uint16_t)modswitch(sa * wa[k] + sb * wb[k]);
       const uint32_t bbar = modswitch(jb.cst + sa * wa[n] + sb * wb[n]);
       const uint32_t shift = (2u * kN - bbar) & (2u * kN - 1);
       // ACC_0 = 0, ACC_1 = X^-bbar testv
-      for (int k = tid; k < kN; k += kCons * 32)
+      for (int k = tid; k < kN; k += kConsThreads)
         A[k] = h == 0 ? 0u : ((((uint32_t)k - shift) & (2u * kN - 1)) < (uint32_t)kN ? kMu : 0u - kMu);
-      named_bar(1, kCons * 32);
+      named_bar(1, kConsThreads);
 
       for (int i = 0; i < n; ++i, ++cm) {
         // gadget digits of X^a ACC_h - ACC_h
         const uint32_t a = abar[i];
-        for (int k = tid; k < kN; k += kCons * 32) {
-          const uint32_t j = ((uint32_t)k - a) & 2047u;
-          uint32_t v = A[j & 1023u];
-          v = (j & 1024u) ? 0u - v : v;
-          const uint32_t y = v - A[k] + kDecOffset;
-          D[k] = (y >> 25) | ((y >> 10) & 0x7F00u) | ((y << 5) & 0x7F0000u);
-        }
-        named_bar(1, kCons * 32);
-        uint32_t x[32];
-        const uint32_t sel = 0x4440u | (uint32_t)rr;
+        for (int k = tid; k < 256; k += kConsThreads) {
+          uint32_t pk[4];  // bytes 0, 1, 2: digits of rows 0, 1, 2 at position k + 256 m
 #pragma unroll
-        for (int e = 0; e < 32; ++e) x[e] = __byte_perm(D[lane + 32 * e], 0u, sel);
-        ntt_fwd<true>(x, myscr, tw1f, tw2f, pr, lane);
+          for (int m = 0; m < 4; ++m) {
+            const uint32_t pos = (uint32_t)k + 256u * m;
+            const uint32_t j = (pos - a) & 2047u;
+            uint32_t v = A[j & 1023u];
+            v = (j & 1024u) ? 0u - v : v;
+            const uint32_t y = v - A[pos] + kDecOffset;
+            pk[m] = (y >> 25) | ((y >> 10) & 0x7F00u) | ((y << 5) & 0x7F0000u);
+          }
+#pragma unroll
+          for (int r = 0; r < 3; ++r) {
+            const uint32_t sel = (uint32_t)r | ((4u + r) << 4);
+            D[r * 256 + k] = __byte_perm(__byte_perm(pk[0], pk[1], sel), __byte_perm(pk[2], pk[3], sel), 0x5410u);
+          }
+        }
+        named_bar(1, kConsThreads);
+        // digit bytes u = d + 64 of row rr; the first stage (distance 512) on load
+        uint32_t x[16];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const uint32_t d4 = D[rr * 256 + lane + 32 * e];  // positions p, p + 256, p + 512, p + 768
+#pragma unroll
+          for (int g = 0; g < 2; ++g) {
+            const uint32_t u = __byte_perm(d4, 0u, 0x4440u | g);
+            const uint32_t t = shoup_mul(z1.x, z1.y, __byte_perm(d4, 0u, 0x4442u | g), pr.q);
+            x[e + 8 * g] = w ? u - t + pr.q2 + pr.dd : u + t + pr.dc;
+          }
+        }
+        fwd_half(x, myscr, tw1f, tw2f, twh, w, pr, lane);
         const uint32_t jc = (it * (uint32_t)n + (uint32_t)i) * 3u + (uint32_t)rr;
         const uint32_t slot = jc % kStages;
-        mbar_wait<false>(full + slot, (jc / kStages) & 1u, abort_flag, args.status);
+        mbar_wait(full + slot, (jc / kStages) & 1u, abort_flag, args.status);
+        // key row layout: position 32 L + E at word ((E >> 2) * 32 + L) * 4 + (E & 3)
         const uint4 *Bown = reinterpret_cast<const uint4 *>(ring + slot * kChunkWords + (h * 2 + P) * kN);
         const uint4 *Both = reinterpret_cast<const uint4 *>(ring + slot * kChunkWords + ((1 - h) * 2 + P) * kN);
-        // row rr's products for both outputs; row `lane` of a product holds
-        // positions 32 lane + e, as 16-byte chunks swizzled by lane
         uint4 *own = reinterpret_cast<uint4 *>(sums + (P * 3 + rr) * kN);
         uint4 *oth = reinterpret_cast<uint4 *>(sums + ((2 + P) * 3 + rr) * kN);
 #pragma unroll
-        for (int e4 = 0; e4 < 8; ++e4) {
-          const uint4 b0 = Bown[e4 * 32 + lane];
-          const uint4 b1 = Both[e4 * 32 + lane];
-          const int chunk = lane * 8 + (e4 ^ (lane & 7));
-          own[chunk] = make_uint4(mont_mul(x[4 * e4 + 0], b0.x, pr), mont_mul(x[4 * e4 + 1], b0.y, pr),
-                                  mont_mul(x[4 * e4 + 2], b0.z, pr), mont_mul(x[4 * e4 + 3], b0.w, pr));
-          oth[chunk] = make_uint4(mont_mul(x[4 * e4 + 0], b1.x, pr), mont_mul(x[4 * e4 + 1], b1.y, pr),
-                                  mont_mul(x[4 * e4 + 2], b1.z, pr), mont_mul(x[4 * e4 + 3], b1.w, pr));
+        for (int c = 0; c < 4; ++c) {
+          const int kidx = (4 * (fb & 1) + c) * 32 + 16 * w + (fb >> 1);
+          const uint4 b0 = Bown[kidx];
+          const uint4 b1 = Both[kidx];
+          const int chunk = 128 * w + (swp(16 * fb + 4 * c) >> 2);
+          own[chunk] = make_uint4(mont_mul(x[4 * c + 0], b0.x, pr), mont_mul(x[4 * c + 1], b0.y, pr),
+                                  mont_mul(x[4 * c + 2], b0.z, pr), mont_mul(x[4 * c + 3], b0.w, pr));
+          oth[chunk] = make_uint4(mont_mul(x[4 * c + 0], b1.x, pr), mont_mul(x[4 * c + 1], b1.y, pr),
+                                  mont_mul(x[4 * c + 2], b1.z, pr), mont_mul(x[4 * c + 3], b1.w, pr));
         }
         __syncwarp();
         if (lane == 0) mbar_arrive_cta(empty + slot);
-        named_bar(2 + P, 96);  // the three rows of prime P in place
+        named_bar(2 + P, kConsThreads / 2);  // the three rows of prime P in place
         {
-          // output 1-h: add the three rows over chunks rr, rr + 3, ... and send them
+          // output 1-h: add the three rows over this warp's chunks and send them
           const uint4 *o0 = reinterpret_cast<const uint4 *>(sums + ((2 + P) * 3) * kN);
-          const uint32_t rslot = map_peer(smem_u32(slots + ((cm & 1u) * 2 + P) * kN), peer);
-          for (int c = rr * 32 + lane; c < 256; c += 96) {
-            const uint4 u = o0[c], v = o0[256 + c], w = o0[512 + c];
-            st_remote_v4(rslot + (uint32_t)c * 16u,
-                         make_uint4(u.x + v.x + w.x, u.y + v.y + w.y, u.z + v.z + w.z, u.w + v.w + w.w));
+          uint32_t *st = stage + ((cm & 1u) * 2 + P) * kN;
+          uint4 *st4 = reinterpret_cast<uint4 *>(st);
+          for (int c = c0 + lane; c < c0 + nc; c += 32) {
+            const uint4 u = o0[c], v = o0[256 + c], t = o0[512 + c];
+            st4[c] = make_uint4(u.x + v.x + t.x, u.y + v.y + t.y, u.z + v.z + t.z, u.w + v.w + t.w);
           }
+          fence_proxy_async_smem();
           __syncwarp();
-          if (lane == 0) mbar_arrive_cluster(done_remote);
+          if (lane == 0)
+            bulk_s2peer(map_peer(smem_u32(slots + ((cm & 1u) * 2 + P) * kN + c0 * 4), peer), st + c0 * 4,
+                        (uint32_t)nc * 16u, map_peer(smem_u32(done + (cm & 1u)), peer));
         }
-        if (rr == 0) {
-          // owner of output h in prime P: the three local rows and the peer's sum
-          mbar_wait<true>(done, cm & 1u, abort_flag, args.status);
+        if (rr < 2) {
+          // quarter Qd of output h in prime P: three local rows and the peer's sum
+          if (warp == 0 && lane == 0) mbar_expect_tx(done + (cm & 1u), kPeerBytes);
+          mbar_wait(done + (cm & 1u), (cm >> 1) & 1u, abort_flag, args.status);
+          uint32_t y[8];
 #pragma unroll
-          for (int e = 0; e < 32; ++e) x[e] = 0u;
+          for (int e = 0; e < 8; ++e) y[e] = 0u;
 #pragma unroll
           for (int r4 = 0; r4 < 4; ++r4) {
-            const uint4 *sl = reinterpret_cast<const uint4 *>(
-                r4 < 3 ? sums + (P * 3 + r4) * kN : slots + ((cm & 1u) * 2 + P) * kN);
+            const uint4 *sl = reinterpret_cast<const uint4 *>(r4 < 3 ? sums + (P * 3 + r4) * kN
+                                                                     : slots + ((cm & 1u) * 2 + P) * kN);
 #pragma unroll
-            for (int c = 0; c < 8; ++c) {
-              const uint4 v = sl[lane * 8 + (c ^ (lane & 7))];
-              x[4 * c + 0] += v.x;
-              x[4 * c + 1] += v.y;
-              x[4 * c + 2] += v.z;
-              x[4 * c + 3] += v.w;
+            for (int c = 0; c < 2; ++c) {
+              const uint4 v = sl[128 * (Qd >> 1) + (swp(256 * (Qd & 1) + 8 * lane + 4 * c) >> 2)];
+              y[4 * c + 0] += v.x;
+              y[4 * c + 1] += v.y;
+              y[4 * c + 2] += v.z;
+              y[4 * c + 3] += v.w;
             }
           }
-          ntt_inv(x, myscr, tw1i, tw2i, twist, pr, lane);
+          inv_quarter(y, myscr, tw1i, tw2i, pr, lane);
           __syncwarp();
 #pragma unroll
-          for (int e = 0; e < 32; ++e) myscr[e * 32 + lane] = x[e];  // natural position lane + 32 e
+          for (int e = 0; e < 8; ++e) myscr[lane + 32 * e] = y[e];  // natural positions of the quarter
         }
-        named_bar(1, kCons * 32);  // both primes' results posted
+        named_bar(1, kConsThreads);  // both primes' quarters posted
         {
-          const uint32_t *r0 = scratch, *r1 = scratch + kXpose;  // owner warps 0 (prime 0) and 1 (prime 1)
-          for (int k = tid; k < kN; k += kCons * 32) A[k] += crt_torus(r0[k], r1[k]);
+          // last two inverse stages, twist, CRT: outputs k + 256 m
+          const uint4 *fin0 = args.tg->fin[0], *fin1 = args.tg->fin[1];
+          for (int k = tid; k < kN / 4; k += kConsThreads) {
+            uint32_t u[4], o0[4], o1[4];
+#pragma unroll
+            for (int Q = 0; Q < 4; ++Q) u[Q] = post0[Q][k];
+            inv_last(o0, u, __ldg(fin0 + 2 * k), __ldg(fin0 + 2 * k + 1), args.tc.psi512[0], args.tc.psi256[0], kQ0);
+#pragma unroll
+            for (int Q = 0; Q < 4; ++Q) u[Q] = post0[Q][k + 2 * kHalf];
+            inv_last(o1, u, __ldg(fin1 + 2 * k), __ldg(fin1 + 2 * k + 1), args.tc.psi512[1], args.tc.psi256[1], kQ1);
+#pragma unroll
+            for (int m = 0; m < 4; ++m) A[k + 256 * m] += crt_torus(o0[m], o1[m]);
+          }
         }
-        named_bar(1, kCons * 32);  // ACC_h updated
+        named_bar(1, kConsThreads);  // ACC_h updated
       }
       // sample extraction: CTA 0 holds the mask a' (from ACC_0), CTA 1 the body b'
       uint32_t *o = args.out + (size_t)tile * kOutStride;
       if (h == 0) {
-        for (int k = tid; k < kN; k += kCons * 32) o[k] = k == 0 ? A[0] : 0u - A[kN - k];
+        for (int k = tid; k < kN; k += kConsThreads) o[k] = k == 0 ? A[0] : 0u - A[kN - k];
       } else if (tid == 0) {
         o[kN] = A[0];
       }
-      named_bar(1, kCons * 32);
+      named_bar(1, kConsThreads);
     }
   }
   __syncwarp();

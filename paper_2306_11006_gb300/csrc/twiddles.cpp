@@ -6,6 +6,18 @@
 // spectrum, omega = psi^2): the stage of half-length h uses omega^-(j 512 / h) for
 // the j-th pair of each block, followed by the twist psi^-p at output p.  Every
 // entry carries its Shoup companion floor(w 2^32 / q).
+//
+// Split transforms of the cluster kernel.  Forward: two warps per transform, half
+// w holds positions 512 w .. 512 w + 511; in pass 2 lane l holds the 16
+// positions of block b = 2 (l mod 16) + l / 16, and stage s (length 8 >> s),
+// block-part c < 2^s uses zeta[(64 << s) + (32 << s) w + (1 << s) b + c].
+// Inverse: four warps per transform (quarters Q of 256 spectral positions), the
+// last two stages and the twist folded together: with u_Q the quarters'
+// outputs at k < 256 and t = (psi^-k u_0, psi^-5k u_1, psi^-3k u_2, psi^-7k u_3),
+//   out_k       = t0 + t1 + t2 + t3
+//   out_(k+512) = psi^-512 (t0 + t1 - t2 - t3)
+//   out_(k+256) = psi^-256 ((t0 - t1) + psi^-512 (t2 - t3))
+//   out_(k+768) = psi^-256 (psi^-512 (t0 - t1) + (t2 - t3)).
 #include <cstdint>
 #include <stdexcept>
 
@@ -76,6 +88,22 @@ void fill(int P, uint64_t q, TwiddleConst *tc, TwiddleGlobal *tg) {
       for (int lane = 0; lane < 32; ++lane)
         tg->inv2[P][(hr - 1 + b) * 32 + lane] = entry(pw(omega_inv, (uint64_t)(lane + 32 * b) * (512 / h), q), q);
   }
+  for (int w = 0; w < 2; ++w)
+    for (int s = 0; s < 4; ++s)
+      for (int c = 0; c < (1 << s); ++c)
+        for (int lane = 0; lane < 32; ++lane) {
+          const int b = 2 * (lane & 15) + (lane >> 4);
+          tg->fwdh[P][w][((1 << s) - 1 + c) * 32 + lane] =
+              entry(zeta[(64 << s) + (32 << s) * w + (1 << s) * b + c], q);
+        }
+  for (int k = 0; k < 256; ++k) {
+    const uint2 t0 = entry(pw(psi_inv, k, q), q), t1 = entry(pw(psi_inv, 5 * k, q), q);
+    const uint2 t2 = entry(pw(psi_inv, 3 * k, q), q), t3 = entry(pw(psi_inv, 7 * k, q), q);
+    tg->fin[P][2 * k] = make_uint4(t0.x, t0.y, t1.x, t1.y);
+    tg->fin[P][2 * k + 1] = make_uint4(t2.x, t2.y, t3.x, t3.y);
+  }
+  tc->psi512[P] = entry(pw(psi_inv, 512, q), q);
+  tc->psi256[P] = entry(pw(psi_inv, 256, q), q);
   // output twist psi^-p at p = lane + 32 e
   for (int e = 0; e < 32; ++e)
     for (int lane = 0; lane < 32; ++lane) tg->twist[P][e * 32 + lane] = entry(pw(psi_inv, lane + 32 * e, q), q);
