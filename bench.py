@@ -366,6 +366,8 @@ def main():
 
     # roofline of the dominant kernel (blind rotation), timed launch by launch
     br_ms, ks_ms, br_l, ks_l = plan.profile(ct_in)
+    br_kernels = sorted({"br_cluster_kernel" if H == 12 else f"br_kernel<{H},{GT}>"
+                         for H, GT, jobs in plan.shapes() if jobs})
     ops = boots * n * MODMUL_PER_CMUX
     achieved = ops / (br_ms / 1e3) / 1e12
     launches_per_step = br_l + ks_l + (1 if len(nl.outputs) else 0)
@@ -386,7 +388,7 @@ def main():
                 "d2h_bytes_per_step": int(len(nl.outputs) * (n + 1) * 4),
                 "p50_ms": 1e3 * float(np.percentile(e2e_s, 50))},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TMODMUL, "unit": "Tmodmul/s",
-                     "frac": achieved / ALU_PEAK_TMODMUL, "traffic": None, "kernel": "br_kernel",
+                     "frac": achieved / ALU_PEAK_TMODMUL, "traffic": None, "kernel": " + ".join(br_kernels),
                      "kernel_ms_per_step": br_ms, "ks_ms_per_step": ks_ms},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,

@@ -152,6 +152,13 @@ int arx_plan_run(int plan, const uint32_t *ct_in, uint32_t *ct_out, void *stream
 int arx_plan_destroy(int plan);
 /* Describe a plan: waves, blind rotations, gates (any may be NULL). */
 int arx_plan_info(int plan, uint32_t *waves, uint64_t *bootstraps, uint64_t *gates);
+/* Launch shape of each wave of a plan (what the autotuner or the override
+ * chose when the plan was created): for wave w < min(cap, waves), H[w] and
+ * GT[w] as in arx_set_launch_shape ((12, 1): the two-CTA cluster kernel) and
+ * jobs[w] = its blind rotations (0 for a wave of linear gates only, which
+ * launches no blind rotation).  Host arrays; any may be NULL.  Returns the
+ * number of waves.  No counterpart in the paper: introspection only. */
+int arx_plan_shapes(int plan, uint32_t *H, uint32_t *GT, uint32_t *jobs, uint32_t cap);
 /* Copy wires of the plan's most recent evaluation: out[k] = wire ids[k]
  * ([count][n+1]; ids host array, out host or device).  Synchronous.  Lets a
  * caller inspect or checkpoint intermediate ciphertexts. */

@@ -57,6 +57,7 @@ SIGNATURES = {
     "arx_plan_run": (_i, [_i, _vp, _vp, _vp]),
     "arx_plan_destroy": (_i, [_i]),
     "arx_plan_info": (_i, [_i, _vp, _vp, _vp]),
+    "arx_plan_shapes": (_i, [_i, _vp, _vp, _vp, _u32]),
     "arx_plan_wires": (_i, [_i, _vp, _sz, _vp]),
     "arx_set_launch_shape": (_i, [_i, _i]),
     "arx_plan_profile": (_i, [_i, _vp, _vp, _vp, _vp, _vp]),
@@ -220,6 +221,13 @@ class Plan:
         out = np.zeros((len(ids), n + 1), np.uint32)
         _check(lib().arx_plan_wires(self.id, _ptr(ids), len(ids), _ptr(out)))
         return out
+
+    def shapes(self):
+        """Launch shape of every wave: list of (H, GT, blind rotations)."""
+        cap = max(self.waves, 1)
+        H, GT, J = (np.zeros(cap, np.uint32) for _ in range(3))
+        w = _check(lib().arx_plan_shapes(self.id, _ptr(H), _ptr(GT), _ptr(J), cap))
+        return [(int(H[k]), int(GT[k]), int(J[k])) for k in range(min(w, cap))]
 
     def profile(self, ct_in):
         """One wave-by-wave run timed per launch: (br_ms, ks_ms, br_launches, ks_launches)."""

@@ -53,6 +53,19 @@ __device__ __forceinline__ PrimeRT prime_rt(int P, const TwiddleConst &tc) {
   return r;
 }
 
+// ---- device-side launch timing (autotuner) --------------------------------
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void stamp_start(unsigned long long *stamps) {
+  if (stamps) atomicMin(stamps, global_ns());
+}
+__device__ __forceinline__ void stamp_end(unsigned long long *stamps) {
+  if (stamps) atomicMax(stamps + 1, global_ns());
+}
+
 // ---- modular helpers ----------------------------------------------------
 // Shoup: w * y mod q in [0, 2q) for any 32-bit y, given wp = floor(w 2^32 / q).
 __device__ __forceinline__ uint32_t shoup_mul(uint32_t w, uint32_t wp, uint32_t y, uint32_t q) {

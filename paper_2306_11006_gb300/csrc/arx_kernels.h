@@ -66,6 +66,7 @@ struct BrArgs {
   uint32_t *out;          // [num_jobs][1028] extracted LWE_N samples
   const TwiddleGlobal *tg;
   unsigned int *status;   // device status word (kDevTimeout on a watchdog expiry)
+  unsigned long long *stamps;  // optional {first CTA start, last warp end} in global-timer ns (autotuner)
   TwiddleConst tc;        // warp-uniform twiddles, read from the parameter bank
 };
 

@@ -316,6 +316,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   cluster_sync_all();  // both CTAs initialised before any remote access
+  if (threadIdx.x == 0) stamp_start(args.stamps);
 
   const int n = args.n;
   const int nclusters = gridDim.x / 2, cid = blockIdx.x / 2;
@@ -506,6 +507,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
   }
   __syncwarp();
   cluster_sync_all();  // neither CTA leaves while the peer may still touch its shared memory
+  if (threadIdx.x == 0) stamp_end(args.stamps);
 }
 
 }  // namespace brc

@@ -360,6 +360,7 @@ __global__ void __launch_bounds__((2 * H * GT + 1) * 32, 1) br_kernel(const __gr
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
+  if (threadIdx.x == 0) stamp_start(args.stamps);
   if (args.num_jobs <= 0) return;
 
   if (warp == kCons) {  // producer: stream BSK rows into the ring
@@ -393,6 +394,7 @@ __global__ void __launch_bounds__((2 * H * GT + 1) * 32, 1) br_kernel(const __gr
   }
   const int g = warp / (2 * H), role = warp % (2 * H);
   br_consumer<H, GT>(S, args, g, role >> 1, role & 1, lane);
+  if (lane == 0) stamp_end(args.stamps);
 }
 
 template <int H, int GT>

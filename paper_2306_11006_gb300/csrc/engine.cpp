@@ -237,9 +237,10 @@ int calibrate(Engine &E, int n) {
   CK(cudaMemset(wires.p, 0, (size_t)kWireStride * 4 * 2));
   std::vector<BrJob> hj(max_jobs, BrJob{0, 1, ARX_MU, 1, 1});
   CK(cudaMemcpy(jobs.p, hj.data(), sizeof(BrJob) * max_jobs, cudaMemcpyHostToDevice));
-  cudaEvent_t a, b;
-  CK(cudaEventCreate(&a));
-  CK(cudaEventCreate(&b));
+  // device-side timing (global timer, first CTA start to last warp end): free of
+  // launch overhead and of anything a profiler adds around a launch
+  DevBuf stamps;
+  CK(stamps.reserve(2 * sizeof(unsigned long long)));
   E.policy.tune.clear();
   for (BrShape s : kShapes) {
     if (!E.policy.occupancy(s)) continue;
@@ -253,15 +254,17 @@ int calibrate(Engine &E, int n) {
     args.tg = E.tg;
     args.status = E.status;
     args.tc = E.tc;
+    args.stamps = stamps.as<unsigned long long>();
     const int grid = E.policy.grid(s, args.num_jobs);
-    float best = 1e30f;
+    double best = 1e30;
     for (int rep = 0; rep < 3; ++rep) {
-      CK(cudaEventRecord(a, E.stream));
+      CK(cudaMemsetAsync(stamps.p, 0xFF, sizeof(unsigned long long), E.stream));
+      CK(cudaMemsetAsync(stamps.as<unsigned long long>() + 1, 0, sizeof(unsigned long long), E.stream));
       CK(launch_br(args, s, grid, E.stream));
-      CK(cudaEventRecord(b, E.stream));
-      CK(cudaEventSynchronize(b));
-      float ms = 0;
-      CK(cudaEventElapsedTime(&ms, a, b));
+      unsigned long long t[2] = {0, 0};
+      CK(cudaMemcpyAsync(t, stamps.p, sizeof(t), cudaMemcpyDeviceToHost, E.stream));
+      CK(cudaStreamSynchronize(E.stream));
+      const double ms = t[1] > t[0] ? (t[1] - t[0]) * 1e-6 : 1e30;
       if (rep) best = std::min(best, ms);
     }
     TuneEntry t;
@@ -270,8 +273,7 @@ int calibrate(Engine &E, int n) {
     t.gates_per_wave = args.num_jobs;
     E.policy.tune.push_back(t);
   }
-  cudaEventDestroy(a);
-  cudaEventDestroy(b);
+  stamps.release();
   bsk.release();
   wires.release();
   jobs.release();
@@ -804,6 +806,19 @@ extern "C" int arx_plan_info(int plan, uint32_t *waves, uint64_t *bootstraps, ui
   if (bootstraps) *bootstraps = P.bootstraps;
   if (gates) *gates = P.num_gates;
   return ARX_OK;
+}
+
+extern "C" int arx_plan_shapes(int plan, uint32_t *H, uint32_t *GT, uint32_t *jobs, uint32_t cap) {
+  API_BEGIN
+  if (plan < 0 || plan >= (int)E.plans.size() || !E.plans[plan]) return fail(ARX_EINVAL, "no plan %d", plan);
+  const Plan &P = *E.plans[plan];
+  for (size_t w = 0; w < P.levels.size() && w < cap; ++w) {
+    const Level &L = P.levels[w];
+    if (H) H[w] = (uint32_t)L.shape.H;
+    if (GT) GT[w] = (uint32_t)L.shape.GT;
+    if (jobs) jobs[w] = (uint32_t)L.br_cnt;
+  }
+  return (int)P.levels.size();
 }
 
 extern "C" int arx_plan_wires(int plan, const uint32_t *ids, size_t count, uint32_t *out) {

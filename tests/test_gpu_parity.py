@@ -199,6 +199,23 @@ def test_graph_mode_equals_plain_mode(O, keys630, gpu630):
     assert np.array_equal(arx.client_decrypt(630, keys630.s, a), nl.plain_eval(bits))
 
 
+def test_plan_shapes_report_every_wave(gpu630):
+    nl = I.union([I.ripple_carry_adder(8), I.array_multiplier(4)])
+    wave, depth = arx.levelize(nl)
+    with arx.Plan(nl, mode=arx.MODE_PLAIN) as p:
+        sh = p.shapes()
+        assert len(sh) == p.waves == depth
+        assert sum(j for _, _, j in sh) == p.bootstraps
+        # narrow waves take the two-CTA cluster kernel under the heuristic
+        assert all(H == 12 and GT == 1 for H, GT, j in sh if 0 < j <= arx.device_sms() // 2)
+    arx.set_launch_shape(6, 1)
+    try:
+        with arx.Plan(nl, mode=arx.MODE_PLAIN) as p:
+            assert all((H, GT) == (6, 1) for H, GT, j in p.shapes() if j)
+    finally:
+        arx.set_launch_shape(0, 0)
+
+
 def _sampled_gate_parity(O, keys, nl, plan, per_level=8, levels=3, seed=0):
     wave, depth = arx.levelize(nl)
     rng = np.random.default_rng(seed)
