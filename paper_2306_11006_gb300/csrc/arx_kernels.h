@@ -39,6 +39,7 @@ struct TwiddleGlobal {
   uint2 twist[2][32 * 32];  // inverse output twist psi^-p, p = lane + 32 e: [e][lane]
   // split transforms of the cluster kernel
   uint2 fwdh[2][2][15 * 32];  // forward pass 2 of half w: [prime][w][(2^s - 1) + block][lane]
+  uint2 fwdq[2][4][7 * 32];   // forward pass 2 of quarter Q: [prime][Q][(2^s - 1) + block][lane]
   uint4 fin[2][512];          // split inverse, last two stages + twist, k < 256:
                               // [2k] = {psi^-k, psi^-5k}, [2k+1] = {psi^-3k, psi^-7k}, with companions
 };
@@ -116,6 +117,12 @@ constexpr int kClusterH = 12;
 size_t br_cluster_smem();
 cudaError_t launch_br_cluster(const BrArgs &args, int clusters, cudaStream_t st);
 int br_cluster_occupancy();  // co-resident clusters on the device (0: cannot launch)
+// Cluster shape {kCluster4H, 1}: one gate on a cluster of four CTAs (four SMs).
+constexpr int kCluster4H = 24;
+size_t br_cluster4_smem();
+cudaError_t launch_br_cluster4(const BrArgs &args, int clusters, cudaStream_t st);
+int br_cluster4_occupancy();
+inline bool is_cluster_shape(BrShape s) { return s.H == kClusterH || s.H == kCluster4H; }
 
 // per-shape launchers (one translation unit per H)
 cudaError_t launch_br_h1(const BrArgs &args, int GT, int grid, cudaStream_t st);

@@ -1,0 +1,244 @@
+// br_cluster_common.cuh -- device helpers shared by the cluster blind-rotation
+// kernels (two-CTA and four-CTA): cluster and mbarrier primitives, bulk copies
+// between CTAs, the CRT recombination, and the split inverse transform.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "arx_device.cuh"
+
+namespace arx {
+namespace clu {
+
+constexpr long long kWaitCycles = 4000000000ll;  // bound of every mbarrier wait (about 2 s)
+// rounding half of the 21-bit gadget plus the +64 offset of each 7-bit digit
+constexpr uint32_t kDecOffset = (1u << 10) + (64u << 25) + (64u << 18) + (64u << 11);
+
+constexpr uint32_t pow_mod(uint64_t b, uint64_t e, uint64_t m) {
+  uint64_t r = 1;
+  b %= m;
+  while (e) {
+    if (e & 1) r = r * b % m;
+    b = b * b % m;
+    e >>= 1;
+  }
+  return (uint32_t)r;
+}
+constexpr uint32_t kQ0InvQ1 = pow_mod(kQ0, kQ1 - 2, kQ1);
+constexpr uint32_t kQ0InvQ1Shoup = (uint32_t)(((uint64_t)kQ0InvQ1 << 32) / kQ1);
+constexpr uint64_t kM = (uint64_t)kQ0 * kQ1;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+__device__ __forceinline__ uint32_t map_peer(uint32_t saddr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+  return r;
+}
+
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// Bulk copy from this CTA's shared memory into a peer CTA's shared memory; the
+// bytes complete on the peer's mbarrier.  Both addresses 16-byte aligned, size a
+// multiple of 16.
+__device__ __forceinline__ void bulk_s2peer(uint32_t dst_cluster, const void *src, uint32_t bytes,
+                                            uint32_t bar_cluster) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          dst_cluster),
+      "r"(smem_u32(src)), "r"(bytes), "r"(bar_cluster)
+      : "memory");
+}
+
+// Orders this thread's generic-proxy writes to shared memory before later
+// async-proxy (bulk copy) reads of them.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_arrive_cta(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
+                                          unsigned int *status) {
+  if (*abort_flag) return false;
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (*abort_flag) return false;
+    if (clock64() - t0 > kWaitCycles) {
+      *abort_flag = 1;
+      atomicOr(status, kDevTimeout);
+      return false;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void named_bar(int id, int threads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
+}
+
+__device__ __forceinline__ uint32_t modswitch(uint32_t x) { return (x + (1u << 20)) >> 21; }
+
+__device__ __forceinline__ uint32_t crt_torus(uint32_t x0, uint32_t x1) {
+  const uint32_t d = x1 + 2u * kQ1 - x0;
+  const uint32_t k = csub(shoup_mul(kQ0InvQ1, kQ0InvQ1Shoup, d, kQ1), kQ1);
+  const uint32_t r = kQ0 * k + x0;
+  return k >= kQ1 / 2 ? r - (uint32_t)kM : r;
+}
+
+// Word offset of position p in a buffer of 32-word rows: the 16-byte chunks of
+// row p >> 5 are XOR-swizzled by the row index (see swz), so that storing 32
+// consecutive positions, and 128-bit loads of 16 (or 8) consecutive positions per
+// lane with the block order below, are free of bank conflicts.
+__device__ __forceinline__ int swp(int p) { return swz(p >> 5, p & 31); }
+
+// Butterfly between lanes (partner lane ^ mask): the lower lane holds x, the
+// upper lane y; returns x + z y or x - z y + 2q.
+__device__ __forceinline__ uint32_t xlane_bfly(uint32_t v, uint2 z, bool upper, int mask, const PrimeRT &pr) {
+  const uint32_t o = __shfl_xor_sync(0xffffffffu, v, mask);
+  const uint32_t y = upper ? v : o, x = upper ? o : v;
+  const uint32_t t = shoup_mul(z.x, z.y, y, pr.q);
+  return upper ? x - t + pr.q2 : x + t;
+}
+
+// Inverse quarter transform (cyclic Cooley-Tukey DIT with omega^-1) of spectral
+// positions 256 Q .. 256 Q + 255, all stages but the last two (half-lengths
+// 1 .. 128).  In: x[e] = position 256 Q + 8 lane + e (< 12 q).  Out: x[e] =
+// position lane + 32 e of the quarter's natural-order result (< 28 q).
+__device__ __forceinline__ void inv_quarter(uint32_t (&x)[8], uint32_t *xbuf, const uint2 *tw1,
+                                            const uint2 *__restrict__ tw2, const PrimeRT &pr, int lane) {
+#pragma unroll
+  for (int t = 0; t < 3; ++t) {  // half-lengths 1, 2, 4: bits 0 .. 2 of e
+    const int hh = 1 << t;
+#pragma unroll
+    for (int e = 0; e < 8; ++e)
+      if ((e & hh) == 0) ct_bfly(x[e], x[e + hh], tw1[(hh - 1) + (e & (hh - 1))], pr);
+  }
+  {  // half-length 8: lane bit 0, omega^-(64 e)
+    const bool up = (lane & 1) != 0;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) x[e] = xlane_bfly(x[e], tw1[7 + e], up, 1, pr);
+  }
+  {  // half-length 16: lane bit 1, omega^-(32 (8 (lane & 1) + e))
+    const bool up = (lane & 2) != 0, odd = (lane & 1) != 0;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const uint2 za = tw1[15 + e], zb = tw1[23 + e];
+      x[e] = xlane_bfly(x[e], odd ? zb : za, up, 2, pr);
+    }
+  }
+  __syncwarp();
+  uint4 *xb4 = reinterpret_cast<uint4 *>(xbuf);
+#pragma unroll
+  for (int c = 0; c < 2; ++c)
+    xb4[swp(8 * lane + 4 * c) >> 2] = make_uint4(x[4 * c], x[4 * c + 1], x[4 * c + 2], x[4 * c + 3]);
+  __syncwarp();
+#pragma unroll
+  for (int e = 0; e < 8; ++e) x[e] = xbuf[swp(lane + 32 * e)];
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {  // half-lengths 32, 64, 128: bits 0 .. 2 of e
+    const int hr = 1 << s;
+#pragma unroll
+    for (int e = 0; e < 8; ++e)
+      if ((e & hr) == 0) ct_bfly(x[e], x[e + hr], __ldg(tw2 + ((hr - 1) + (e & (hr - 1))) * 32 + lane), pr);
+  }
+}
+
+// Last two inverse stages, output twist and full reduction for one prime:
+// outputs k, k + 256, k + 512, k + 768 from the quarters' outputs u_Q at k.
+__device__ __forceinline__ void inv_last(uint32_t (&o)[4], const uint32_t (&u)[4], uint4 f01, uint4 f23,
+                                         uint2 m512, uint2 m256, uint32_t q) {
+  const uint32_t t0 = shoup_mul(f01.x, f01.y, u[0], q), t1 = shoup_mul(f01.z, f01.w, u[1], q);
+  const uint32_t t2 = shoup_mul(f23.x, f23.y, u[2], q), t3 = shoup_mul(f23.z, f23.w, u[3], q);
+  const uint32_t s01 = t0 + t1, d01 = t0 - t1 + 2u * q, s23 = t2 + t3, d23 = t2 - t3 + 2u * q;  // < 4q
+  o[0] = csub(csub(csub(s01 + s23, 4u * q), 2u * q), q);
+  o[2] = csub(shoup_mul(m512.x, m512.y, s01 - s23 + 4u * q, q), q);
+  const uint32_t e23 = shoup_mul(m512.x, m512.y, d23, q), e01 = shoup_mul(m512.x, m512.y, d01, q);
+  o[1] = csub(shoup_mul(m256.x, m256.y, d01 + e23, q), q);
+  o[3] = csub(shoup_mul(m256.x, m256.y, e01 + d23, q), q);
+}
+
+// Gadget digits of X^a ACC - ACC (Fig. 2), packed for the split forward
+// transforms: D[r][k] holds the digit bytes d + 64 of row r at positions k,
+// k + 256, k + 512, k + 768 (bytes 0 .. 3).
+__device__ __forceinline__ void make_digits4(uint32_t *D, const uint32_t *A, uint32_t a, int tid, int nthreads) {
+  for (int k = tid; k < 256; k += nthreads) {
+    uint32_t pk[4];  // bytes 0, 1, 2: digits of rows 0, 1, 2 at position k + 256 m
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const uint32_t pos = (uint32_t)k + 256u * m;
+      const uint32_t j = (pos - a) & 2047u;
+      uint32_t v = A[j & 1023u];
+      v = (j & 1024u) ? 0u - v : v;
+      const uint32_t y = v - A[pos] + kDecOffset;
+      pk[m] = (y >> 25) | ((y >> 10) & 0x7F00u) | ((y << 5) & 0x7F0000u);
+    }
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const uint32_t sel = (uint32_t)r | ((4u + r) << 4);
+      D[r * 256 + k] = __byte_perm(__byte_perm(pk[0], pk[1], sel), __byte_perm(pk[2], pk[3], sel), 0x5410u);
+    }
+  }
+}
+
+// Last two inverse stages, twist and CRT of both primes, then ACC += the
+// Torus32 result: post0[Q] holds quarter Q of prime 0 in natural order, prime 1
+// lies poff1 words above it.
+__device__ __forceinline__ void crt_update(uint32_t *A, const uint32_t *const (&post0)[4], int poff1,
+                                           const BrArgs &args, int tid, int nthreads) {
+  const uint4 *fin0 = args.tg->fin[0], *fin1 = args.tg->fin[1];
+  for (int k = tid; k < kN / 4; k += nthreads) {
+    uint32_t u[4], o0[4], o1[4];
+#pragma unroll
+    for (int Q = 0; Q < 4; ++Q) u[Q] = post0[Q][k];
+    inv_last(o0, u, __ldg(fin0 + 2 * k), __ldg(fin0 + 2 * k + 1), args.tc.psi512[0], args.tc.psi256[0], kQ0);
+#pragma unroll
+    for (int Q = 0; Q < 4; ++Q) u[Q] = post0[Q][k + poff1];
+    inv_last(o1, u, __ldg(fin1 + 2 * k), __ldg(fin1 + 2 * k + 1), args.tc.psi512[1], args.tc.psi256[1], kQ1);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) A[k + 256 * m] += crt_torus(o0[m], o1[m]);
+  }
+}
+
+}  // namespace clu
+}  // namespace arx

@@ -80,6 +80,8 @@ int ensure_init(Engine &E) {
     return fail(ARX_ECUDA, "device %s (sm_%d%d): libarx is built for sm_103a", prop.name, prop.major, prop.minor);
   E.sms = prop.multiProcessorCount;
   E.policy.sms = E.sms;
+  E.policy.clusters4 = E.policy.occupancy(BrShape{kCluster4H, 1});
+  E.policy.clusters2 = E.policy.occupancy(BrShape{kClusterH, 1});
   E.smem_optin = prop.sharedMemPerBlockOptin;
   std::unique_ptr<TwiddleGlobal> tg(new TwiddleGlobal);
   make_twiddles(&E.tc, tg.get());
@@ -172,7 +174,7 @@ void emit_gate(uint32_t type, uint32_t w0, uint32_t w1, uint32_t w2, uint32_t ou
 // --------------------------------------------------------------------------
 // launch shapes: heuristic and autotuned
 // --------------------------------------------------------------------------
-const BrShape kShapes[] = {{kClusterH, 1}, {6, 1}, {3, 1}, {3, 2}, {2, 1}, {2, 3}, {1, 1}, {1, 2}, {1, 4}, {1, 6}};
+const BrShape kShapes[] = {{kCluster4H, 1}, {kClusterH, 1}, {6, 1}, {3, 1}, {3, 2}, {2, 1}, {2, 3}, {1, 1}, {1, 2}, {1, 4}, {1, 6}};
 
 int ShapePolicy::occupancy(BrShape s) {
   for (auto &kv : occ)
@@ -182,11 +184,14 @@ int ShapePolicy::occupancy(BrShape s) {
   return o;
 }
 
-// Plain mode: a two-SM cluster per gate while the wave leaves SMs idle, then about
-// twelve consumer warps per SM with more gates per CTA as the wave widens.
+// Plain mode: a four-SM, then a two-SM cluster per gate while all of the wave's
+// clusters fit on the device at once (four-CTA clusters pack less densely: a
+// cluster must sit in one GPC), then about twelve consumer warps per SM with more
+// gates per CTA as the wave widens.
 BrShape ShapePolicy::heuristic(int jobs) const {
   if (forced.H) return forced;
-  if (jobs <= sms / 2) return {kClusterH, 1};
+  if (jobs <= clusters4) return {kCluster4H, 1};
+  if (jobs <= std::max(clusters2, sms / 2)) return {kClusterH, 1};
   const int per_sm = (jobs + sms - 1) / sms;
   if (per_sm <= 1) return {6, 1};
   if (per_sm == 2) return {3, 2};
@@ -212,9 +217,9 @@ BrShape ShapePolicy::pick(int jobs, int n) const {
   return out;
 }
 
-// Grid of a launch: CTAs, or clusters for the cluster shape.
+// Grid of a launch: CTAs, or clusters for the cluster shapes.
 int ShapePolicy::grid(BrShape s, int jobs) {
-  if (s.H == kClusterH) return std::max(1, std::min(jobs, std::max(1, occupancy(s))));
+  if (is_cluster_shape(s)) return std::max(1, std::min(jobs, std::max(1, occupancy(s))));
   const int tiles = (jobs + s.GT - 1) / s.GT;
   const int cap = sms * std::max(1, occupancy(s));
   return std::max(1, std::min(tiles, cap));
@@ -227,7 +232,7 @@ int calibrate(Engine &E, int n) {
   if (E.policy.tuned_n == n) return ARX_OK;
   const int ncal = std::min(n, 16);
   int max_jobs = 0;
-  for (BrShape s : kShapes) max_jobs = std::max(max_jobs, s.H == kClusterH ? E.policy.occupancy(s) : E.sms * s.GT * std::max(1, E.policy.occupancy(s)));
+  for (BrShape s : kShapes) max_jobs = std::max(max_jobs, is_cluster_shape(s) ? E.policy.occupancy(s) : E.sms * s.GT * std::max(1, E.policy.occupancy(s)));
   DevBuf bsk, wires, jobs, out;
   CK(bsk.reserve((size_t)ncal * 6 * kChunkBytes));
   CK(wires.reserve((size_t)kWireStride * 4 * 2));
@@ -248,7 +253,7 @@ int calibrate(Engine &E, int n) {
     args.bsk = bsk.as<uint32_t>();
     args.wires = wires.as<uint32_t>();
     args.jobs = jobs.as<BrJob>();
-    args.num_jobs = s.H == kClusterH ? E.policy.occupancy(s) : E.sms * s.GT * E.policy.occupancy(s);
+    args.num_jobs = is_cluster_shape(s) ? E.policy.occupancy(s) : E.sms * s.GT * E.policy.occupancy(s);
     args.n = ncal;
     args.out = out.as<uint32_t>();
     args.tg = E.tg;

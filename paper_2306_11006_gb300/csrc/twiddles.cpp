@@ -18,6 +18,10 @@
 //   out_(k+512) = psi^-512 (t0 + t1 - t2 - t3)
 //   out_(k+256) = psi^-256 ((t0 - t1) + psi^-512 (t2 - t3))
 //   out_(k+768) = psi^-256 (psi^-512 (t0 - t1) + (t2 - t3)).
+// The four-CTA kernel also splits the forward transform in quarters Q (the
+// first two stages taken on load): in pass 2 lane l holds the 8 positions of
+// block b = 4 (l mod 8) + l / 8, and stage s (length 4 >> s), block-part c < 2^s
+// uses zeta[(128 << s) + (32 << s) Q + (1 << s) b + c].
 #include <cstdint>
 #include <stdexcept>
 
@@ -95,6 +99,14 @@ void fill(int P, uint64_t q, TwiddleConst *tc, TwiddleGlobal *tg) {
           const int b = 2 * (lane & 15) + (lane >> 4);
           tg->fwdh[P][w][((1 << s) - 1 + c) * 32 + lane] =
               entry(zeta[(64 << s) + (32 << s) * w + (1 << s) * b + c], q);
+        }
+  for (int Q = 0; Q < 4; ++Q)
+    for (int s = 0; s < 3; ++s)
+      for (int c = 0; c < (1 << s); ++c)
+        for (int lane = 0; lane < 32; ++lane) {
+          const int b = 4 * (lane & 7) + (lane >> 3);
+          tg->fwdq[P][Q][((1 << s) - 1 + c) * 32 + lane] =
+              entry(zeta[(128 << s) + (32 << s) * Q + (1 << s) * b + c], q);
         }
   for (int k = 0; k < 256; ++k) {
     const uint2 t0 = entry(pw(psi_inv, k, q), q), t1 = entry(pw(psi_inv, 5 * k, q), q);
