@@ -39,9 +39,9 @@ struct TwiddleGlobal {
   uint2 twist[2][32 * 32];  // inverse output twist psi^-p, p = lane + 32 e: [e][lane]
   // split transforms of the cluster kernel
   uint2 fwdh[2][2][15 * 32];  // forward pass 2 of half w: [prime][w][(2^s - 1) + block][lane]
-  uint2 fwdq[2][4][7 * 32];   // forward pass 2 of quarter Q: [prime][Q][(2^s - 1) + block][lane]
-  uint4 fin[2][512];          // split inverse, last two stages + twist, k < 256:
-                              // [2k] = {psi^-k, psi^-5k}, [2k+1] = {psi^-3k, psi^-7k}, with companions
+  uint2 fwdc[2][4][7 * 32];   // forward middle pass of quarter Q (lengths 32, 16, 8): [prime][Q][(2^s - 1) + block][lane]
+  uint2 fwdq[2][4][7 * 32];   // forward last pass of quarter Q (lengths 4, 2, 1): [prime][Q][(2^s - 1) + block][lane]
+  uint2 fint[2][4][256];      // split inverse, twist of quarter Q at k < 256: psi^-(c_Q k), c = (1, 5, 3, 7)
 };
 
 enum : uint32_t {

@@ -8,8 +8,9 @@
 // forward 1024-point transform is split over two warps (halves w = 0, 1): its
 // first stage (distance 512) is taken while loading the digits, after which the
 // halves are independent 512-point transforms.  Each inverse transform is split
-// over four warps (quarters of the spectrum), whose last two stages and the
-// output twist are folded into the CRT pass that all warps share.  So twelve
+// over four warps (quarters of the spectrum, each applying its part of the
+// output twist); the last two stages are folded into the CRT pass that all warps
+// share.  So twelve
 // consumer warps per CTA: (row, prime, half); eight of them run the inverses.
 //
 // Each warp writes its key products for both outputs to local shared memory;
@@ -280,6 +281,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
             }
           }
           inv_quarter(y, myscr, tw1i, tw2i, pr, lane);
+          quarter_twist(y, args.tg->fint[P][Qd], pr, lane);
           __syncwarp();
 #pragma unroll
           for (int e = 0; e < 8; ++e) myscr[lane + 32 * e] = y[e];  // natural positions of the quarter

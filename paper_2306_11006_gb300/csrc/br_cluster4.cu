@@ -13,10 +13,10 @@
 // output 1-h are summed over the rows and moved by the bulk copy engine to CTA
 // (1-h, w) (4 KiB); with the products it receives, the CTA holds half w of both
 // primes' sums of output h and runs their inverse quarters (all stages but the
-// last two) on four warps.  It sends those quarters to CTA (h, 1-w) (4 KiB) and
-// receives the other two, so both CTAs of component h run the folded last stages,
-// the twist and the CRT on all four quarters and update identical copies of
-// ACC_h.  Every cross-CTA dependency is a transaction count on an mbarrier
+// last two, then the output twist) on four warps.  It sends those quarters to
+// CTA (h, 1-w) (4 KiB) and receives the other two, so both CTAs of component h
+// run the folded last stages and the CRT on all four quarters and update
+// identical copies of ACC_h.  Every cross-CTA dependency is a transaction count on an mbarrier
 // (double-buffered by CMux parity); every wait is bounded.
 #include <cuda_runtime.h>
 
@@ -57,34 +57,49 @@ constexpr size_t kSmem = kRingBytes + kAccBytes + kDigBytes + kRowBytes + kSlotB
 // key loads and the product stores conflict-free).
 __device__ __forceinline__ int fwd_block8(int lane) { return 4 * (lane & 7) + (lane >> 3); }
 
+// Word offset of position p (0 .. 255) for the first transpose of the forward
+// quarter: bits 3-4 XORed with bits 6-7, so that storing a[lane + 32 e] and
+// loading a[(lane mod 8) + 8 e + 64 (lane / 8)] (one e per access) are free of
+// bank conflicts.
+__device__ __forceinline__ int sw1(int p) { return p ^ (((p >> 6) & 3) << 3); }
+
 // Forward quarter transform (negacyclic Cooley-Tukey, merged twist), spectral
-// block Qf (positions 256 Qf + p).  In: x[e] = the output of the first two
-// stages at p = lane + 32 e (< 5q + 128).  Out: x[e] = spectral position
-// 256 Qf + 8 b + e, b = fwd_block8(lane) (< 22q), bit-reversed order.
+// block Qf (positions 256 Qf + p), in three register passes joined by two
+// shared-memory transposes.  In: x[e] = the output of the first two stages at
+// p = lane + 32 e (< 5q + 128).  Out: x[e] = spectral position 256 Qf + 8 b + e,
+// b = fwd_block8(lane) (< 22q), bit-reversed order.
 __device__ __forceinline__ void fwd_quarter(uint32_t (&x)[8], uint32_t *xbuf, const uint2 *tw1,
-                                            const uint2 *__restrict__ tw2, const uint2 *__restrict__ twq, int Qf,
+                                            const uint2 *__restrict__ twc, const uint2 *__restrict__ twq, int Qf,
                                             const PrimeRT &pr, int lane) {
 #pragma unroll
-  for (int s = 0; s < 3; ++s) {  // lengths 128, 64, 32: bits 2 .. 0 of e
+  for (int s = 0; s < 2; ++s) {  // lengths 128, 64 on a[lane + 32 e]: bits 2, 1 of e
     const int lr = 4 >> s, m = 4 << s;
 #pragma unroll
     for (int e = 0; e < 8; ++e)
       if ((e & lr) == 0) ct_bfly(x[e], x[e + lr], tw1[m + (m >> 2) * Qf + e / (2 * lr)], pr);
   }
-  {  // length 16: lane bit 4, zeta[32 + 8 Qf + e]
-    const bool up = (lane & 16) != 0;
+  const int pc = (lane & 7) + 64 * (lane >> 3);  // middle pass: position pc + 8 e
+  __syncwarp();
 #pragma unroll
-    for (int e = 0; e < 8; ++e) x[e] = xlane_bfly(x[e], __ldg(tw2 + 8 * Qf + e), up, 16, pr);
-  }
-  {  // length 8: lane bit 3, zeta[64 + 16 Qf + 2 e + lane / 16]
-    const bool up = (lane & 8) != 0;
-    const uint2 *t8 = tw2 + (1 + (lane >> 4)) * 32 + 8 * Qf;
+  for (int e = 0; e < 8; ++e) xbuf[sw1(lane + 32 * e)] = x[e];
+  __syncwarp();
 #pragma unroll
-    for (int e = 0; e < 8; ++e) x[e] = xlane_bfly(x[e], __ldg(t8 + e), up, 8, pr);
+  for (int e = 0; e < 8; ++e) x[e] = xbuf[sw1(pc + 8 * e)];
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {  // lengths 32, 16, 8: bits 2 .. 0 of e, per-lane twiddles
+    const int lr = 4 >> s, k0 = (1 << s) - 1;
+    uint2 z;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      if ((e & lr) == 0) {
+        if ((e & (2 * lr - 1)) == 0) z = __ldg(twc + (k0 + e / (2 * lr)) * 32 + lane);
+        ct_bfly(x[e], x[e + lr], z, pr);
+      }
+    }
   }
   __syncwarp();
 #pragma unroll
-  for (int e = 0; e < 8; ++e) xbuf[swp(lane + 32 * e)] = x[e];
+  for (int e = 0; e < 8; ++e) xbuf[swp(pc + 8 * e)] = x[e];
   __syncwarp();
   const uint4 *xb4 = reinterpret_cast<const uint4 *>(xbuf);
   const int b = fwd_block8(lane);
@@ -97,7 +112,7 @@ __device__ __forceinline__ void fwd_quarter(uint32_t (&x)[8], uint32_t *xbuf, co
     x[4 * c + 3] = v.w;
   }
 #pragma unroll
-  for (int s = 0; s < 3; ++s) {  // lengths 4, 2, 1 with per-lane twiddles
+  for (int s = 0; s < 3; ++s) {  // lengths 4, 2, 1 on a[8 b + e], per-lane twiddles
     const int len = 4 >> s, k0 = (1 << s) - 1;
     uint2 z;
 #pragma unroll
@@ -185,7 +200,7 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(kThreads, 1)
     const PrimeRT pr = prime_rt(P, args.tc);
     uint32_t *myscr = scratch + warp * kQuarter;
     const uint2 *tw1f = args.tc.fwd1[P], *tw1i = args.tc.inv1[P];
-    const uint2 *tw2f = args.tg->fwd2[P], *tw2i = args.tg->inv2[P], *twq = args.tg->fwdq[P][Qf];
+    const uint2 *tw2i = args.tg->inv2[P], *twc = args.tg->fwdc[P][Qf], *twq = args.tg->fwdq[P][Qf];
     const uint2 z1 = args.tc.fwd1[P][1], z23 = args.tc.fwd1[P][2 + (Qf >> 1)];
     // chunks [c0, c0 + nc) of a prime's half-row sum are this warp's to send
     const int c0 = (rr * 2 + v) * 22, nc = c0 + 22 <= 128 ? 22 : 128 - c0;
@@ -223,7 +238,7 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(kThreads, 1)
           const uint32_t t2 = shoup_mul(z23.x, z23.y, b, pr.q);
           x[e] = (Qf & 1) ? a - t2 + pr.q2 : a + t2;
         }
-        fwd_quarter(x, myscr, tw1f, tw2f, twq, Qf, pr, lane);
+        fwd_quarter(x, myscr, tw1f, twc, twq, Qf, pr, lane);
         const uint32_t jc = (it * (uint32_t)n + (uint32_t)i) * 3u + (uint32_t)rr;
         const uint32_t slot = jc % kStages;
         mbar_wait(full + slot, (jc / kStages) & 1u, abort_flag, args.status);
@@ -289,6 +304,7 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(kThreads, 1)
             }
           }
           inv_quarter(y, myscr, tw1i, tw2i, pr, lane);
+          quarter_twist(y, args.tg->fint[P][Qf], pr, lane);
           // post the quarter here and at CTA (h, 1-w)
           uint32_t *pq = post + ((par * 2 + P) * 4 + Qf) * kQuarter;
 #pragma unroll

@@ -184,13 +184,24 @@ __device__ __forceinline__ void inv_quarter(uint32_t (&x)[8], uint32_t *xbuf, co
   }
 }
 
+// Twist of quarter Q's inverse outputs before they are posted: x[e] (position
+// k = lane + 32 e, < 28q) -> psi^-(c_Q k) x[e] in [0, 2q), c = (1, 5, 3, 7).
+__device__ __forceinline__ void quarter_twist(uint32_t (&x)[8], const uint2 *__restrict__ fint, const PrimeRT &pr,
+                                              int lane) {
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    const uint2 f = __ldg(fint + lane + 32 * e);
+    x[e] = shoup_mul(f.x, f.y, x[e], pr.q);
+  }
+}
+
 // Last two inverse stages, output twist and full reduction for one prime:
-// outputs k, k + 256, k + 512, k + 768 from the quarters' outputs u_Q at k.
-__device__ __forceinline__ void inv_last(uint32_t (&o)[4], const uint32_t (&u)[4], uint4 f01, uint4 f23,
-                                         uint2 m512, uint2 m256, uint32_t q) {
-  const uint32_t t0 = shoup_mul(f01.x, f01.y, u[0], q), t1 = shoup_mul(f01.z, f01.w, u[1], q);
-  const uint32_t t2 = shoup_mul(f23.x, f23.y, u[2], q), t3 = shoup_mul(f23.z, f23.w, u[3], q);
-  const uint32_t s01 = t0 + t1, d01 = t0 - t1 + 2u * q, s23 = t2 + t3, d23 = t2 - t3 + 2u * q;  // < 4q
+// outputs k, k + 256, k + 512, k + 768 from the twisted quarter outputs
+// t = (psi^-k u_0, psi^-5k u_1, psi^-3k u_2, psi^-7k u_3) at k, each in [0, 2q).
+__device__ __forceinline__ void inv_last(uint32_t (&o)[4], const uint32_t (&t)[4], uint2 m512, uint2 m256,
+                                         uint32_t q) {
+  const uint32_t s01 = t[0] + t[1], d01 = t[0] - t[1] + 2u * q;  // < 4q
+  const uint32_t s23 = t[2] + t[3], d23 = t[2] - t[3] + 2u * q;
   o[0] = csub(csub(csub(s01 + s23, 4u * q), 2u * q), q);
   o[2] = csub(shoup_mul(m512.x, m512.y, s01 - s23 + 4u * q, q), q);
   const uint32_t e23 = shoup_mul(m512.x, m512.y, d23, q), e01 = shoup_mul(m512.x, m512.y, d01, q);
@@ -221,20 +232,19 @@ __device__ __forceinline__ void make_digits4(uint32_t *D, const uint32_t *A, uin
   }
 }
 
-// Last two inverse stages, twist and CRT of both primes, then ACC += the
-// Torus32 result: post0[Q] holds quarter Q of prime 0 in natural order, prime 1
+// Last two inverse stages and CRT of both primes, then ACC += the Torus32
+// result: post0[Q] holds quarter Q of prime 0 (twisted, natural order), prime 1
 // lies poff1 words above it.
 __device__ __forceinline__ void crt_update(uint32_t *A, const uint32_t *const (&post0)[4], int poff1,
                                            const BrArgs &args, int tid, int nthreads) {
-  const uint4 *fin0 = args.tg->fin[0], *fin1 = args.tg->fin[1];
   for (int k = tid; k < kN / 4; k += nthreads) {
-    uint32_t u[4], o0[4], o1[4];
+    uint32_t t[4], o0[4], o1[4];
 #pragma unroll
-    for (int Q = 0; Q < 4; ++Q) u[Q] = post0[Q][k];
-    inv_last(o0, u, __ldg(fin0 + 2 * k), __ldg(fin0 + 2 * k + 1), args.tc.psi512[0], args.tc.psi256[0], kQ0);
+    for (int Q = 0; Q < 4; ++Q) t[Q] = post0[Q][k];
+    inv_last(o0, t, args.tc.psi512[0], args.tc.psi256[0], kQ0);
 #pragma unroll
-    for (int Q = 0; Q < 4; ++Q) u[Q] = post0[Q][k + poff1];
-    inv_last(o1, u, __ldg(fin1 + 2 * k), __ldg(fin1 + 2 * k + 1), args.tc.psi512[1], args.tc.psi256[1], kQ1);
+    for (int Q = 0; Q < 4; ++Q) t[Q] = post0[Q][k + poff1];
+    inv_last(o1, t, args.tc.psi512[1], args.tc.psi256[1], kQ1);
 #pragma unroll
     for (int m = 0; m < 4; ++m) A[k + 256 * m] += crt_torus(o0[m], o1[m]);
   }

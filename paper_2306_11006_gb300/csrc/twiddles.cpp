@@ -19,9 +19,11 @@
 //   out_(k+256) = psi^-256 ((t0 - t1) + psi^-512 (t2 - t3))
 //   out_(k+768) = psi^-256 (psi^-512 (t0 - t1) + (t2 - t3)).
 // The four-CTA kernel also splits the forward transform in quarters Q (the
-// first two stages taken on load): in pass 2 lane l holds the 8 positions of
-// block b = 4 (l mod 8) + l / 8, and stage s (length 4 >> s), block-part c < 2^s
-// uses zeta[(128 << s) + (32 << s) Q + (1 << s) b + c].
+// first two stages taken on load).  Its middle pass holds positions
+// (l mod 8) + 8 e + 64 g, g = l / 8: stage s (length 32 >> s), block-part c < 2^s
+// uses zeta[(16 << s) + (4 << s) Q + (1 << s) g + c].  In its last pass lane l
+// holds the 8 positions of block b = 4 (l mod 8) + l / 8, and stage s (length
+// 4 >> s) uses zeta[(128 << s) + (32 << s) Q + (1 << s) b + c].
 #include <cstdint>
 #include <stdexcept>
 
@@ -107,13 +109,12 @@ void fill(int P, uint64_t q, TwiddleConst *tc, TwiddleGlobal *tg) {
           const int b = 4 * (lane & 7) + (lane >> 3);
           tg->fwdq[P][Q][((1 << s) - 1 + c) * 32 + lane] =
               entry(zeta[(128 << s) + (32 << s) * Q + (1 << s) * b + c], q);
+          tg->fwdc[P][Q][((1 << s) - 1 + c) * 32 + lane] =
+              entry(zeta[(16 << s) + (4 << s) * Q + (1 << s) * (lane >> 3) + c], q);
         }
-  for (int k = 0; k < 256; ++k) {
-    const uint2 t0 = entry(pw(psi_inv, k, q), q), t1 = entry(pw(psi_inv, 5 * k, q), q);
-    const uint2 t2 = entry(pw(psi_inv, 3 * k, q), q), t3 = entry(pw(psi_inv, 7 * k, q), q);
-    tg->fin[P][2 * k] = make_uint4(t0.x, t0.y, t1.x, t1.y);
-    tg->fin[P][2 * k + 1] = make_uint4(t2.x, t2.y, t3.x, t3.y);
-  }
+  const int cQ[4] = {1, 5, 3, 7};
+  for (int Q = 0; Q < 4; ++Q)
+    for (int k = 0; k < 256; ++k) tg->fint[P][Q][k] = entry(pw(psi_inv, (uint64_t)cQ[Q] * k, q), q);
   tc->psi512[P] = entry(pw(psi_inv, 512, q), q);
   tc->psi256[P] = entry(pw(psi_inv, 256, q), q);
   // output twist psi^-p at p = lane + 32 e
