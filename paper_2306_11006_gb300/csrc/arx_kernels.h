@@ -41,6 +41,7 @@ struct TwiddleGlobal {
   uint2 fwdh[2][2][15 * 32];  // forward pass 2 of half w: [prime][w][(2^s - 1) + block][lane]
   uint2 fwdc[2][4][7 * 32];   // forward middle pass of quarter Q (lengths 32, 16, 8): [prime][Q][(2^s - 1) + block][lane]
   uint2 fwdq[2][4][7 * 32];   // forward last pass of quarter Q (lengths 4, 2, 1): [prime][Q][(2^s - 1) + block][lane]
+  uint2 invc[2][7 * 32];      // inverse quarter, middle pass (half-lengths 8, 16, 32): [prime][(2^s - 1) + j][lane]
   uint2 fint[2][4][256];      // split inverse, twist of quarter Q at k < 256: psi^-(c_Q k), c = (1, 5, 3, 7)
 };
 

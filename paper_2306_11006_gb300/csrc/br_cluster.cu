@@ -280,7 +280,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
               y[4 * c + 3] += v.w;
             }
           }
-          inv_quarter(y, myscr, tw1i, tw2i, pr, lane);
+          inv_quarter(y, myscr, tw1i, args.tg->invc[P], tw2i, pr, lane);
           quarter_twist(y, args.tg->fint[P][Qd], pr, lane);
           __syncwarp();
 #pragma unroll

@@ -9,9 +9,10 @@
 // Per CMux: the first two forward stages (distances 512 and 256) are taken while
 // loading the packed digits, after which the four quarters of a transform are
 // independent 256-point transforms; the CTA runs its two quarters of the three
-// rows in both primes on twelve warps (row, prime, quarter).  Key products for
-// output 1-h are summed over the rows and moved by the bulk copy engine to CTA
-// (1-h, w) (4 KiB); with the products it receives, the CTA holds half w of both
+// rows in both primes on twelve warps (row, prime, quarter).  Each warp adds its
+// key products for output 1-h into CTA (1-h, w)'s receive slot with a bulk
+// reduction (1 KiB; the receiver zeroes the slot after use); with the products
+// it receives, the CTA holds half w of both
 // primes' sums of output h and runs their inverse quarters (all stages but the
 // last two, then the output twist) on four warps.  It sends those quarters to
 // CTA (h, 1-w) (4 KiB) and receives the other two, so both CTAs of component h
@@ -36,32 +37,26 @@ constexpr int kStages = 4;                  // ring of 16 KiB key rows
 constexpr int kAbarPitch = 640;
 constexpr int kHalfW = 512;                 // words of a half spectrum
 constexpr int kQuarter = 256;
-constexpr uint32_t kPeerBytes = 2 * kHalfW * 4;       // row sums of half w, both primes
+constexpr uint32_t kPeerBytes = kCons * kQuarter * 4;  // the peer's twelve product quarters
 constexpr uint32_t kPartnerBytes = 2 * 2 * kQuarter * 4;  // two inverse quarters, both primes
 
 // shared memory (bytes)
 constexpr size_t kRingBytes = (size_t)kStages * kChunkBytes;
 constexpr size_t kAccBytes = kN * 4;                 // ACC_h
 constexpr size_t kDigBytes = 3 * 256 * 4;            // [row][k] digit bytes of k, k+256, k+512, k+768
-constexpr size_t kRowBytes = 2 * 2 * 3 * kHalfW * 4; // [output own/other][prime][row][half w]
+constexpr size_t kOwnBytes = 2 * 3 * kHalfW * 4;     // [prime][row][half w] products for output h
+constexpr size_t kOthBytes = 2 * 2 * 3 * kHalfW * 4; // [parity][prime][row][half w] products for output 1-h
 constexpr size_t kSlotBytes = 2 * 2 * kHalfW * 4;    // [parity][prime][half w] the peer's row sums
-constexpr size_t kStageBytes = 2 * 2 * kHalfW * 4;   // [parity][prime][half w] row sums sent
 constexpr size_t kPostBytes = 2 * 2 * 4 * kQuarter * 4;  // [parity][prime][quarter][k] inverse quarters
 constexpr size_t kScrBytes = (size_t)kCons * kQuarter * 4;
 constexpr size_t kAbarBytes = kAbarPitch * 2;
 constexpr size_t kBarBytes = (2 * kStages + 4) * 8 + 16;
-constexpr size_t kSmem = kRingBytes + kAccBytes + kDigBytes + kRowBytes + kSlotBytes + kStageBytes + kPostBytes +
+constexpr size_t kSmem = kRingBytes + kAccBytes + kDigBytes + kOwnBytes + kOthBytes + kSlotBytes + kPostBytes +
                          kScrBytes + kAbarBytes + kBarBytes;
 
 // Block of 8 positions that lane l holds after the forward transpose (makes the
 // key loads and the product stores conflict-free).
 __device__ __forceinline__ int fwd_block8(int lane) { return 4 * (lane & 7) + (lane >> 3); }
-
-// Word offset of position p (0 .. 255) for the first transpose of the forward
-// quarter: bits 3-4 XORed with bits 6-7, so that storing a[lane + 32 e] and
-// loading a[(lane mod 8) + 8 e + 64 (lane / 8)] (one e per access) are free of
-// bank conflicts.
-__device__ __forceinline__ int sw1(int p) { return p ^ (((p >> 6) & 3) << 3); }
 
 // Forward quarter transform (negacyclic Cooley-Tukey, merged twist), spectral
 // block Qf (positions 256 Qf + p), in three register passes joined by two
@@ -131,10 +126,10 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(kThreads, 1)
   uint32_t *ring = reinterpret_cast<uint32_t *>(smem);
   uint32_t *A = reinterpret_cast<uint32_t *>(smem + kRingBytes);
   uint32_t *D = A + kN;                          // [row][256]
-  uint32_t *rows = D + 3 * 256;                  // [output own/other][prime][row][512], swizzled (swp)
-  uint32_t *slots = rows + 12 * kHalfW;          // [parity][prime][512], same layout
-  uint32_t *stage = slots + 4 * kHalfW;          // [parity][prime][512], same layout
-  uint32_t *post = stage + 4 * kHalfW;           // [parity][prime][quarter][256], natural order
+  uint32_t *own = D + 3 * 256;                   // [prime][row][512], swizzled (swp)
+  uint32_t *oth = own + 6 * kHalfW;              // [parity][prime][row][512], same layout
+  uint32_t *slots = oth + 12 * kHalfW;           // [parity][prime][512], same layout, zero between uses
+  uint32_t *post = slots + 4 * kHalfW;           // [parity][prime][quarter][256], natural order
   uint32_t *scratch = post + 16 * kQuarter;      // [warp][256]
   uint16_t *abar = reinterpret_cast<uint16_t *>(scratch + kCons * kQuarter);
   uint64_t *full = reinterpret_cast<uint64_t *>(abar + kAbarPitch);
@@ -159,6 +154,8 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(kThreads, 1)
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  for (int k = threadIdx.x; k < 4 * kHalfW; k += kThreads) slots[k] = 0u;
+  fence_proxy_async_smem();
   cluster_sync_all();  // all four CTAs initialised before any remote access
   if (threadIdx.x == 0) stamp_start(args.stamps);
 
@@ -202,8 +199,6 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(kThreads, 1)
     const uint2 *tw1f = args.tc.fwd1[P], *tw1i = args.tc.inv1[P];
     const uint2 *tw2i = args.tg->inv2[P], *twc = args.tg->fwdc[P][Qf], *twq = args.tg->fwdq[P][Qf];
     const uint2 z1 = args.tc.fwd1[P][1], z23 = args.tc.fwd1[P][2 + (Qf >> 1)];
-    // chunks [c0, c0 + nc) of a prime's half-row sum are this warp's to send
-    const int c0 = (rr * 2 + v) * 22, nc = c0 + 22 <= 128 ? 22 : 128 - c0;
     const int fb = fwd_block8(lane);
     uint32_t it = 0, cm = 0;  // tile counter, CMux counter
     for (int tile = cid; tile < tiles; tile += nclusters, ++it) {
@@ -245,35 +240,26 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(kThreads, 1)
         // key row layout: position 32 L + E at word ((E >> 2) * 32 + L) * 4 + (E & 3)
         const uint4 *Bown = reinterpret_cast<const uint4 *>(ring + slot * kChunkWords + (h * 2 + P) * kN);
         const uint4 *Both = reinterpret_cast<const uint4 *>(ring + slot * kChunkWords + ((1 - h) * 2 + P) * kN);
-        uint4 *own = reinterpret_cast<uint4 *>(rows + (P * 3 + rr) * kHalfW);
-        uint4 *oth = reinterpret_cast<uint4 *>(rows + ((2 + P) * 3 + rr) * kHalfW);
-        // products for the peer's output first, so that their transfer overlaps the rest
+        uint4 *own4 = reinterpret_cast<uint4 *>(own + (P * 3 + rr) * kHalfW);
+        uint32_t *oq = oth + ((par * 2 + P) * 3 + rr) * kHalfW + kQuarter * v;  // quarter v of this row
+        uint4 *oth4 = reinterpret_cast<uint4 *>(oth + ((par * 2 + P) * 3 + rr) * kHalfW);
+        // products for the peer's output first: added into its slot while the rest runs
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
           const uint4 b1 = Both[(2 * (fb & 3) + c) * 32 + 8 * Qf + (fb >> 2)];
-          oth[swp(256 * v + 8 * fb + 4 * c) >> 2] =
+          oth4[swp(256 * v + 8 * fb + 4 * c) >> 2] =
               make_uint4(mont_mul(x[4 * c + 0], b1.x, pr), mont_mul(x[4 * c + 1], b1.y, pr),
                          mont_mul(x[4 * c + 2], b1.z, pr), mont_mul(x[4 * c + 3], b1.w, pr));
         }
-        named_bar(2 + P, kConsThreads / 2);  // the three rows of output 1-h, prime P, half w, in place
-        {
-          const uint4 *o0 = reinterpret_cast<const uint4 *>(rows + ((2 + P) * 3) * kHalfW);
-          uint32_t *st = stage + (par * 2 + P) * kHalfW;
-          uint4 *st4 = reinterpret_cast<uint4 *>(st);
-          for (int c = c0 + lane; c < c0 + nc; c += 32) {
-            const uint4 u = o0[c], q = o0[128 + c], t = o0[256 + c];
-            st4[c] = make_uint4(u.x + q.x + t.x, u.y + q.y + t.y, u.z + q.z + t.z, u.w + q.w + t.w);
-          }
-          fence_proxy_async_smem();
-          __syncwarp();
-          if (lane == 0)
-            bulk_s2peer(map_peer(smem_u32(slots + (par * 2 + P) * kHalfW + c0 * 4), peer), st + c0 * 4,
-                        (uint32_t)nc * 16u, map_peer(smem_u32(done1 + par), peer));
-        }
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0)
+          bulk_add_s2peer(map_peer(smem_u32(slots + (par * 2 + P) * kHalfW + kQuarter * v), peer), oq,
+                          kQuarter * 4u, map_peer(smem_u32(done1 + par), peer));
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
           const uint4 b0 = Bown[(2 * (fb & 3) + c) * 32 + 8 * Qf + (fb >> 2)];
-          own[swp(256 * v + 8 * fb + 4 * c) >> 2] =
+          own4[swp(256 * v + 8 * fb + 4 * c) >> 2] =
               make_uint4(mont_mul(x[4 * c + 0], b0.x, pr), mont_mul(x[4 * c + 1], b0.y, pr),
                          mont_mul(x[4 * c + 2], b0.z, pr), mont_mul(x[4 * c + 3], b0.w, pr));
         }
@@ -292,18 +278,20 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(kThreads, 1)
           for (int e = 0; e < 8; ++e) y[e] = 0u;
 #pragma unroll
           for (int r4 = 0; r4 < 4; ++r4) {
-            const uint4 *sl = reinterpret_cast<const uint4 *>(r4 < 3 ? rows + (P * 3 + r4) * kHalfW
-                                                                     : slots + (par * 2 + P) * kHalfW);
+            uint4 *sl = reinterpret_cast<uint4 *>(r4 < 3 ? own + (P * 3 + r4) * kHalfW : slots + (par * 2 + P) * kHalfW);
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
-              const uint4 q = sl[swp(256 * v + 8 * lane + 4 * c) >> 2];
+              const int ci = swp(256 * v + 8 * lane + 4 * c) >> 2;
+              const uint4 q = sl[ci];
               y[4 * c + 0] += q.x;
               y[4 * c + 1] += q.y;
               y[4 * c + 2] += q.z;
               y[4 * c + 3] += q.w;
+              if (r4 == 3) sl[ci] = make_uint4(0u, 0u, 0u, 0u);  // the slot starts its next use at zero
             }
           }
-          inv_quarter(y, myscr, tw1i, tw2i, pr, lane);
+          fence_proxy_async_smem();  // the zeroes precede the peer's next bulk additions
+          inv_quarter(y, myscr, tw1i, args.tg->invc[P], tw2i, pr, lane);
           quarter_twist(y, args.tg->fint[P][Qf], pr, lane);
           // post the quarter here and at CTA (h, 1-w)
           uint32_t *pq = post + ((par * 2 + P) * 4 + Qf) * kQuarter;

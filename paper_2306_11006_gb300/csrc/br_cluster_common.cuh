@@ -59,6 +59,18 @@ __device__ __forceinline__ void bulk_s2peer(uint32_t dst_cluster, const void *sr
       : "memory");
 }
 
+// Bulk element-wise u32 addition of this CTA's shared memory into a peer CTA's
+// shared memory (performed by the bulk copy engine); the bytes complete on the
+// peer's mbarrier.  Both addresses 16-byte aligned, size a multiple of 16.
+__device__ __forceinline__ void bulk_add_s2peer(uint32_t dst_cluster, const void *src, uint32_t bytes,
+                                                uint32_t bar_cluster) {
+  asm volatile(
+      "cp.reduce.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes.add.u32 [%0], [%1], %2, [%3];" ::"r"(
+          dst_cluster),
+      "r"(smem_u32(src)), "r"(bytes), "r"(bar_cluster)
+      : "memory");
+}
+
 // Orders this thread's generic-proxy writes to shared memory before later
 // async-proxy (bulk copy) reads of them.
 __device__ __forceinline__ void fence_proxy_async_smem() {
@@ -141,32 +153,28 @@ __device__ __forceinline__ uint32_t xlane_bfly(uint32_t v, uint2 z, bool upper, 
   return upper ? x - t + pr.q2 : x + t;
 }
 
+// Word offsets for the quarter transposes (positions 0 .. 255): sw1 XORs bits
+// 3-4 with bits 6-7, so that a[lane + 32 e] and a[(lane mod 8) + 8 e +
+// 64 (lane / 8)] (one e per access) are both free of bank conflicts; swp (see
+// above) pairs the latter with 128-bit accesses of 8 consecutive positions.
+__device__ __forceinline__ int sw1(int p) { return p ^ (((p >> 6) & 3) << 3); }
+
 // Inverse quarter transform (cyclic Cooley-Tukey DIT with omega^-1) of spectral
 // positions 256 Q .. 256 Q + 255, all stages but the last two (half-lengths
-// 1 .. 128).  In: x[e] = position 256 Q + 8 lane + e (< 12 q).  Out: x[e] =
-// position lane + 32 e of the quarter's natural-order result (< 28 q).
+// 1 .. 128), in three register passes joined by two shared-memory transposes.
+// In: x[e] = position 256 Q + 8 lane + e (< 12 q).  Out: x[e] = position
+// lane + 32 e of the quarter's natural-order result (< 28 q).
 __device__ __forceinline__ void inv_quarter(uint32_t (&x)[8], uint32_t *xbuf, const uint2 *tw1,
-                                            const uint2 *__restrict__ tw2, const PrimeRT &pr, int lane) {
+                                            const uint2 *__restrict__ twc, const uint2 *__restrict__ tw2,
+                                            const PrimeRT &pr, int lane) {
 #pragma unroll
-  for (int t = 0; t < 3; ++t) {  // half-lengths 1, 2, 4: bits 0 .. 2 of e
+  for (int t = 0; t < 3; ++t) {  // half-lengths 1, 2, 4 on a[8 lane + e]: bits 0 .. 2 of e
     const int hh = 1 << t;
 #pragma unroll
     for (int e = 0; e < 8; ++e)
       if ((e & hh) == 0) ct_bfly(x[e], x[e + hh], tw1[(hh - 1) + (e & (hh - 1))], pr);
   }
-  {  // half-length 8: lane bit 0, omega^-(64 e)
-    const bool up = (lane & 1) != 0;
-#pragma unroll
-    for (int e = 0; e < 8; ++e) x[e] = xlane_bfly(x[e], tw1[7 + e], up, 1, pr);
-  }
-  {  // half-length 16: lane bit 1, omega^-(32 (8 (lane & 1) + e))
-    const bool up = (lane & 2) != 0, odd = (lane & 1) != 0;
-#pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      const uint2 za = tw1[15 + e], zb = tw1[23 + e];
-      x[e] = xlane_bfly(x[e], odd ? zb : za, up, 2, pr);
-    }
-  }
+  const int pc = (lane & 7) + 64 * (lane >> 3);  // middle pass: position pc + 8 e
   __syncwarp();
   uint4 *xb4 = reinterpret_cast<uint4 *>(xbuf);
 #pragma unroll
@@ -174,9 +182,22 @@ __device__ __forceinline__ void inv_quarter(uint32_t (&x)[8], uint32_t *xbuf, co
     xb4[swp(8 * lane + 4 * c) >> 2] = make_uint4(x[4 * c], x[4 * c + 1], x[4 * c + 2], x[4 * c + 3]);
   __syncwarp();
 #pragma unroll
-  for (int e = 0; e < 8; ++e) x[e] = xbuf[swp(lane + 32 * e)];
+  for (int e = 0; e < 8; ++e) x[e] = xbuf[swp(pc + 8 * e)];
 #pragma unroll
-  for (int s = 0; s < 3; ++s) {  // half-lengths 32, 64, 128: bits 0 .. 2 of e
+  for (int s = 0; s < 3; ++s) {  // half-lengths 8, 16, 32: bits 0 .. 2 of e, per-lane twiddles
+    const int hr = 1 << s;
+#pragma unroll
+    for (int e = 0; e < 8; ++e)
+      if ((e & hr) == 0) ct_bfly(x[e], x[e + hr], __ldg(twc + ((hr - 1) + (e & (hr - 1))) * 32 + lane), pr);
+  }
+  __syncwarp();
+#pragma unroll
+  for (int e = 0; e < 8; ++e) xbuf[sw1(pc + 8 * e)] = x[e];
+  __syncwarp();
+#pragma unroll
+  for (int e = 0; e < 8; ++e) x[e] = xbuf[sw1(lane + 32 * e)];
+#pragma unroll
+  for (int s = 1; s < 3; ++s) {  // half-lengths 64, 128 on a[lane + 32 e]: bits 1, 2 of e
     const int hr = 1 << s;
 #pragma unroll
     for (int e = 0; e < 8; ++e)

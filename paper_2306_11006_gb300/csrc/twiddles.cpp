@@ -112,6 +112,13 @@ void fill(int P, uint64_t q, TwiddleConst *tc, TwiddleGlobal *tg) {
           tg->fwdc[P][Q][((1 << s) - 1 + c) * 32 + lane] =
               entry(zeta[(16 << s) + (4 << s) * Q + (1 << s) * (lane >> 3) + c], q);
         }
+  // inverse quarter, middle pass on positions (l mod 8) + 8 e + 64 (l / 8): stage s
+  // (half-length 8 << s) pairs j = (l mod 8) + 8 c, c < 2^s, twiddle omega^-(j 512 / h)
+  for (int s = 0; s < 3; ++s)
+    for (int c = 0; c < (1 << s); ++c)
+      for (int lane = 0; lane < 32; ++lane)
+        tg->invc[P][((1 << s) - 1 + c) * 32 + lane] =
+            entry(pw(omega_inv, (uint64_t)((lane & 7) + 8 * c) * (512 / (8 << s)), q), q);
   const int cQ[4] = {1, 5, 3, 7};
   for (int Q = 0; Q < 4; ++Q)
     for (int k = 0; k < 256; ++k) tg->fint[P][Q][k] = entry(pw(psi_inv, (uint64_t)cQ[Q] * k, q), q);
