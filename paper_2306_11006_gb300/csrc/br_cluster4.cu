@@ -33,7 +33,7 @@ using namespace clu;
 constexpr int kCons = 12;                   // consumer warps: (row 0..2) x (prime 0..1) x (quarter 0..1)
 constexpr int kThreads = (kCons + 1) * 32;  // + producer warp
 constexpr int kConsThreads = kCons * 32;
-constexpr int kStages = 4;                  // ring of 16 KiB key rows
+constexpr int kStages = 6;                  // ring of 16 KiB key rows: two CMux ahead
 constexpr int kAbarPitch = 640;
 constexpr int kHalfW = 512;                 // words of a half spectrum
 constexpr int kQuarter = 256;
