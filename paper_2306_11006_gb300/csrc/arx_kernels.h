@@ -123,7 +123,12 @@ constexpr int kCluster4H = 24;
 size_t br_cluster4_smem();
 cudaError_t launch_br_cluster4(const BrArgs &args, int clusters, cudaStream_t st);
 int br_cluster4_occupancy();
-inline bool is_cluster_shape(BrShape s) { return s.H == kClusterH || s.H == kCluster4H; }
+// Cluster shape {kCluster8H, 1}: one gate on a cluster of eight CTAs (eight SMs).
+constexpr int kCluster8H = 48;
+size_t br_cluster8_smem();
+cudaError_t launch_br_cluster8(const BrArgs &args, int clusters, cudaStream_t st);
+int br_cluster8_occupancy();
+inline bool is_cluster_shape(BrShape s) { return s.H == kClusterH || s.H == kCluster4H || s.H == kCluster8H; }
 
 // per-shape launchers (one translation unit per H)
 cudaError_t launch_br_h1(const BrArgs &args, int GT, int grid, cudaStream_t st);

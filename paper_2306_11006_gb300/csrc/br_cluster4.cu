@@ -54,10 +54,6 @@ constexpr size_t kBarBytes = (2 * kStages + 4) * 8 + 16;
 constexpr size_t kSmem = kRingBytes + kAccBytes + kDigBytes + kOwnBytes + kOthBytes + kSlotBytes + kPostBytes +
                          kScrBytes + kAbarBytes + kBarBytes;
 
-// Block of 8 positions that lane l holds after the forward transpose (makes the
-// key loads and the product stores conflict-free).
-__device__ __forceinline__ int fwd_block8(int lane) { return 4 * (lane & 7) + (lane >> 3); }
-
 // Forward quarter transform (negacyclic Cooley-Tukey, merged twist), spectral
 // block Qf (positions 256 Qf + p), in three register passes joined by two
 // shared-memory transposes.  In: x[e] = the output of the first two stages at
@@ -218,21 +214,8 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(kThreads, 1)
         const uint32_t par = cm & 1u, ph = (cm >> 1) & 1u;
         make_digits4(D, A, abar[i], tid, kConsThreads);
         named_bar(1, kConsThreads);
-        // the first two stages on load: bytes of positions p, p+256, p+512, p+768
         uint32_t x[8];
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const uint32_t d4 = D[rr * 256 + lane + 32 * e];
-          const uint32_t t0 = shoup_mul(z1.x, z1.y, __byte_perm(d4, 0u, 0x4442u), pr.q);
-          const uint32_t t1 = shoup_mul(z1.x, z1.y, __byte_perm(d4, 0u, 0x4443u), pr.q);
-          const uint32_t u0 = __byte_perm(d4, 0u, 0x4440u), u1 = __byte_perm(d4, 0u, 0x4441u);
-          // stage 1 (distance 512): upper spectral half takes the differences
-          const uint32_t a = Qf < 2 ? u0 + t0 + pr.dc : u0 - t0 + pr.q2 + pr.dd;
-          const uint32_t b = Qf < 2 ? u1 + t1 + pr.dc : u1 - t1 + pr.q2 + pr.dd;
-          // stage 2 (distance 256) with zeta[2] or zeta[3]
-          const uint32_t t2 = shoup_mul(z23.x, z23.y, b, pr.q);
-          x[e] = (Qf & 1) ? a - t2 + pr.q2 : a + t2;
-        }
+        load_first2(x, D + rr * 256, z1, z23, Qf, pr, lane);
         fwd_quarter(x, myscr, tw1f, twc, twq, Qf, pr, lane);
         const uint32_t jc = (it * (uint32_t)n + (uint32_t)i) * 3u + (uint32_t)rr;
         const uint32_t slot = jc % kStages;

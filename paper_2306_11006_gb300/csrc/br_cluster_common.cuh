@@ -205,6 +205,31 @@ __device__ __forceinline__ void inv_quarter(uint32_t (&x)[8], uint32_t *xbuf, co
   }
 }
 
+// Block of 8 positions that lane l holds after the forward quarter transform
+// (makes the key loads and the product stores conflict-free).
+__device__ __forceinline__ int fwd_block8(int lane) { return 4 * (lane & 7) + (lane >> 3); }
+
+// The first two forward stages (distances 512 and 256) of spectral quarter Qf,
+// taken while loading packed digit bytes: Dr[k] holds the bytes u = d + 64 of
+// positions k, k+256, k+512, k+768 (one row).  Out: x[e] = the stage-2 output at
+// p = lane + 32 e of the quarter (< 5q + 128); the -64 offsets ride on dc, dd.
+__device__ __forceinline__ void load_first2(uint32_t (&x)[8], const uint32_t *Dr, uint2 z1, uint2 z23, int Qf,
+                                            const PrimeRT &pr, int lane) {
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    const uint32_t d4 = Dr[lane + 32 * e];
+    const uint32_t t0 = shoup_mul(z1.x, z1.y, __byte_perm(d4, 0u, 0x4442u), pr.q);
+    const uint32_t t1 = shoup_mul(z1.x, z1.y, __byte_perm(d4, 0u, 0x4443u), pr.q);
+    const uint32_t u0 = __byte_perm(d4, 0u, 0x4440u), u1 = __byte_perm(d4, 0u, 0x4441u);
+    // stage 1 (distance 512): the upper spectral half takes the differences
+    const uint32_t a = Qf < 2 ? u0 + t0 + pr.dc : u0 - t0 + pr.q2 + pr.dd;
+    const uint32_t b = Qf < 2 ? u1 + t1 + pr.dc : u1 - t1 + pr.q2 + pr.dd;
+    // stage 2 (distance 256) with zeta[2] or zeta[3]
+    const uint32_t t2 = shoup_mul(z23.x, z23.y, b, pr.q);
+    x[e] = (Qf & 1) ? a - t2 + pr.q2 : a + t2;
+  }
+}
+
 // Twist of quarter Q's inverse outputs before they are posted: x[e] (position
 // k = lane + 32 e, < 28q) -> psi^-(c_Q k) x[e] in [0, 2q), c = (1, 5, 3, 7).
 __device__ __forceinline__ void quarter_twist(uint32_t (&x)[8], const uint2 *__restrict__ fint, const PrimeRT &pr,

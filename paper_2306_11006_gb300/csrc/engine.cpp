@@ -80,6 +80,7 @@ int ensure_init(Engine &E) {
     return fail(ARX_ECUDA, "device %s (sm_%d%d): libarx is built for sm_103a", prop.name, prop.major, prop.minor);
   E.sms = prop.multiProcessorCount;
   E.policy.sms = E.sms;
+  E.policy.clusters8 = E.policy.occupancy(BrShape{kCluster8H, 1});
   E.policy.clusters4 = E.policy.occupancy(BrShape{kCluster4H, 1});
   E.policy.clusters2 = E.policy.occupancy(BrShape{kClusterH, 1});
   E.smem_optin = prop.sharedMemPerBlockOptin;
@@ -174,7 +175,7 @@ void emit_gate(uint32_t type, uint32_t w0, uint32_t w1, uint32_t w2, uint32_t ou
 // --------------------------------------------------------------------------
 // launch shapes: heuristic and autotuned
 // --------------------------------------------------------------------------
-const BrShape kShapes[] = {{kCluster4H, 1}, {kClusterH, 1}, {6, 1}, {3, 1}, {3, 2}, {2, 1}, {2, 3}, {1, 1}, {1, 2}, {1, 4}, {1, 6}};
+const BrShape kShapes[] = {{kCluster8H, 1}, {kCluster4H, 1}, {kClusterH, 1}, {6, 1}, {3, 1}, {3, 2}, {2, 1}, {2, 3}, {1, 1}, {1, 2}, {1, 4}, {1, 6}};
 
 int ShapePolicy::occupancy(BrShape s) {
   for (auto &kv : occ)
@@ -184,12 +185,13 @@ int ShapePolicy::occupancy(BrShape s) {
   return o;
 }
 
-// Plain mode: a four-SM, then a two-SM cluster per gate while all of the wave's
-// clusters fit on the device at once (four-CTA clusters pack less densely: a
-// cluster must sit in one GPC), then about twelve consumer warps per SM with more
-// gates per CTA as the wave widens.
+// Plain mode: an eight-, four-, then two-SM cluster per gate while all of the
+// wave's clusters fit on the device at once (larger clusters pack less densely:
+// a cluster must sit in one GPC), then about twelve consumer warps per SM with
+// more gates per CTA as the wave widens.
 BrShape ShapePolicy::heuristic(int jobs) const {
   if (forced.H) return forced;
+  if (jobs <= clusters8) return {kCluster8H, 1};
   if (jobs <= clusters4) return {kCluster4H, 1};
   if (jobs <= std::max(clusters2, sms / 2)) return {kClusterH, 1};
   const int per_sm = (jobs + sms - 1) / sms;

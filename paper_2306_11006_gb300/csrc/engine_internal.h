@@ -65,7 +65,7 @@ struct TuneEntry {
 // serving thread can use a snapshot without the engine lock.
 struct ShapePolicy {
   int sms = 0;
-  int clusters4 = 0, clusters2 = 0;  // co-resident four-CTA / two-CTA clusters (gates per wave)
+  int clusters8 = 0, clusters4 = 0, clusters2 = 0;  // co-resident eight- / four- / two-CTA clusters (gates per wave)
   std::vector<TuneEntry> tune;
   int tuned_n = -1;
   std::vector<std::pair<BrShape, int>> occ;

@@ -214,6 +214,7 @@ cudaError_t launch_gather(const uint32_t *wires, const uint32_t *idx, int count,
 size_t br_smem(BrShape s) {
   if (s.H == kClusterH) return s.GT == 1 ? br_cluster_smem() : 0;
   if (s.H == kCluster4H) return s.GT == 1 ? br_cluster4_smem() : 0;
+  if (s.H == kCluster8H) return s.GT == 1 ? br_cluster8_smem() : 0;
   switch (s.H) {
     case 1: return br_smem_h1(s.GT);
     case 2: return br_smem_h2(s.GT);
@@ -228,6 +229,7 @@ bool br_shape_supported(BrShape s) { return br_smem(s) != 0; }
 int br_occupancy(BrShape s) {
   if (s.H == kClusterH) return s.GT == 1 ? br_cluster_occupancy() : 0;
   if (s.H == kCluster4H) return s.GT == 1 ? br_cluster4_occupancy() : 0;
+  if (s.H == kCluster8H) return s.GT == 1 ? br_cluster8_occupancy() : 0;
   switch (s.H) {
     case 1: return br_occupancy_h1(s.GT);
     case 2: return br_occupancy_h2(s.GT);
@@ -237,12 +239,16 @@ int br_occupancy(BrShape s) {
   }
 }
 
-int br_threads(BrShape s) { return is_cluster_shape(s) ? 13 * 32 : (2 * s.H * s.GT + 1) * 32; }
+int br_threads(BrShape s) {
+  if (s.H == kCluster8H) return 9 * 32;
+  return is_cluster_shape(s) ? 13 * 32 : (2 * s.H * s.GT + 1) * 32;
+}
 
 cudaError_t launch_br(const BrArgs &args, BrShape s, int grid, cudaStream_t st) {
   if (args.num_jobs <= 0) return cudaSuccess;
   if (s.H == kClusterH) return s.GT == 1 ? launch_br_cluster(args, grid, st) : cudaErrorInvalidValue;
   if (s.H == kCluster4H) return s.GT == 1 ? launch_br_cluster4(args, grid, st) : cudaErrorInvalidValue;
+  if (s.H == kCluster8H) return s.GT == 1 ? launch_br_cluster8(args, grid, st) : cudaErrorInvalidValue;
   switch (s.H) {
     case 1: return launch_br_h1(args, s.GT, grid, st);
     case 2: return launch_br_h2(args, s.GT, grid, st);
