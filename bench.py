@@ -51,7 +51,7 @@ MODMUL_PER_CMUX = 2 * (8 * 5120 + 12 * 1024)
 ALU_PEAK_TMODMUL = 152 * 2.070e9 * 64 / 3 / 1e12
 # DRAM bytes (read + write) per launch from one ncu capture of the current kernel
 # build (profiles/): the key once per launch.  Only kernels listed here report it.
-TRAFFIC_PER_LAUNCH = {"br_cluster4_kernel": 62.08e6 + 0.05e6}
+TRAFFIC_PER_LAUNCH = {"br_cluster8_kernel": 62.09e6 + 0.07e6}
 
 
 def workload(name: str, gates: int = 64):
