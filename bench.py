@@ -269,13 +269,38 @@ def run_serve(args):
         print(json.dumps(line), flush=True)
 
 
+def run_alu(args):
+    """Integer-pipe throughput of this GPU (arx_probe_alu): the measured side of the
+    blind rotation's ALU roofline, next to the derived peak."""
+    from paper_2306_11006_gb300 import arx
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    clk = Clocks(local, os.path.join(ROOT, "gpurun_out", "clocks_alu.csv")) \
+        if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else Clocks(local, "/tmp/arx_clocks_alu.csv")
+    rates = arx.probe_alu()
+    clocks = clk.stop()
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    shoup_t = rates["shoup_bfly_q27"] * sms * mhz * 1e6 / 1e12
+    print(json.dumps({
+        "metric": "integer pipe throughput (lane operations per clock per SM, 32 warps per SM)",
+        "value": rates["shoup_bfly_q27"], "unit": "Shoup butterflies/clk/SM", "n_gpus": 1,
+        "higher_is_better": True, "data": "synthetic", "rates_per_sm_clk": rates,
+        "shoup_bfly_tmodmul_per_s": shoup_t, "derived_peak_tmodmul_per_s": ALU_PEAK_TMODMUL,
+        "goldilocks_vs_crt27_butterflies": rates["goldilocks_bfly"] / (2 * rates["shoup_bfly_q27"]),
+        "sms": sms, "clocks": clocks}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="arx", choices=["arx", "reference"])
-    ap.add_argument("--workload", default="netlists", choices=["netlists", "gates", "gates64", "dag", "matmul", "serve"])
+    ap.add_argument("--workload", default="netlists",
+                    choices=["netlists", "gates", "gates64", "dag", "matmul", "serve", "alu"])
     ap.add_argument("--clients", type=int, default=4, help="serve: clients (key sets)")
     ap.add_argument("--rate", type=float, default=4.0, help="serve: Poisson arrival rate, requests/s")
     ap.add_argument("--requests", type=int, default=32, help="serve: requests per run")
@@ -284,6 +309,11 @@ def main():
     ap.add_argument("--mode", default="graph", choices=["graph", "plain"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
+    if args.workload == "alu":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the integer-pipe probe has no CPU counterpart"}))
+            return
+        return run_alu(args)
     if args.workload == "serve":
         if args.impl == "reference":
             nl, desc = workload("dag")

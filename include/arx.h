@@ -244,6 +244,18 @@ int arx_device_status(void);
 /* Number of SMs of the device in use (0 before the first call that needs it). */
 int arx_device_sms(void);
 
+/* Integer-pipe throughput of the current device, the measured side of the blind
+ * rotation's ALU roofline (no counterpart in the paper).  rate[i], i < count
+ * (at most 7), receives lane operations per clock per SM (32 warps per SM,
+ * independent dependency chains, clock64 timing) for: 0 IMAD, 1 IMAD.HI,
+ * 2 IMAD.WIDE, 3 plain ALU (one unit = IADD3 + SHF + LOP), 4 Shoup butterfly
+ * mod a 27-bit prime,
+ * 5 Montgomery multiply-accumulate mod a 27-bit prime, 6 butterfly mod the
+ * paper's 2^64 - 2^32 + 1 (Sec. 5.4).  Host array.  Synchronous, takes about a
+ * second, allocates and frees a few KB of device memory.  Returns ARX_OK or
+ * ARX_EINVAL / ARX_ECUDA. */
+int arx_probe_alu(double *rate, int count);
+
 /* ------------------------------------------------------- client side ---- */
 /* Key generation, encryption and decryption as the client (the data owner)
  * performs them (App. D: the server only ever sees ciphertexts and public

@@ -71,6 +71,7 @@ SIGNATURES = {
     "arx_last_error": (ctypes.c_char_p, []),
     "arx_device_status": (_i, []),
     "arx_device_sms": (_i, []),
+    "arx_probe_alu": (_i, [_vp, _i]),
     "arx_client_keygen": (_i, [_i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "arx_client_encrypt": (_i, [_i, _vp, _vp, _vp, _vp, _sz, _vp]),
     "arx_client_decrypt": (_i, [_i, _vp, _vp, _sz, _vp]),
@@ -311,6 +312,16 @@ def device_status() -> int:
 
 def device_sms() -> int:
     return lib().arx_device_sms()
+
+
+PROBE_NAMES = ("imad", "imad_hi", "imad_wide", "alu_x3", "shoup_bfly_q27", "mont_mac_q27", "goldilocks_bfly")
+
+
+def probe_alu() -> dict:
+    """Lane operations per clock per SM of the integer pipes (see arx_probe_alu)."""
+    rate = np.zeros(len(PROBE_NAMES), np.float64)
+    _check(lib().arx_probe_alu(_ptr(rate), len(rate)))
+    return dict(zip(PROBE_NAMES, (float(r) for r in rate)))
 
 
 # ------------------------------------------------------------ client side ---
