@@ -54,6 +54,27 @@ ALU_PEAK_TMODMUL = 152 * 2.070e9 * 64 / 3 / 1e12
 TRAFFIC_PER_LAUNCH = {"br_cluster8_kernel": 62.09e6 + 0.07e6}
 
 
+def replica_max_ms(ms: float, world: int, device="cpu") -> float:
+    """The job's time under replicas: the max over ranks of each rank's time."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(units_per_step: int, steps: int, world: int, max_ms: float) -> float:
+    """Whole-job throughput: the units every rank processed over the slowest rank's time."""
+    return units_per_step * steps * world / (max_ms / 1e3)
+
+
+def replica_seed(base: int, rank: int) -> int:
+    """Each replica evaluates its own inputs (no rank shares an input seed)."""
+    return base + rank
+
+
 def workload(name: str, gates: int = 64):
     if name == "netlists":
         return I.union([I.ripple_carry_adder(32), I.array_multiplier(8)], name="adder32+mult8"), \
@@ -342,8 +363,8 @@ def main():
     kr = I.key_randomness(0, n)
     bsk, ksk = arx.client_keygen(kr)
     keyset = arx.load_keys(bsk, ksk, n)
-    bits = I.random_bits(1000 + rank, nl.num_inputs)
-    m, e = I.encryption_randomness(2000 + rank, nl.num_inputs, n)
+    bits = I.random_bits(replica_seed(1000, rank), nl.num_inputs)
+    m, e = I.encryption_randomness(replica_seed(2000, rank), nl.num_inputs, n)
     ct_host = arx.client_encrypt(n, kr.s, m, e, bits)
     ct_in = torch.from_numpy(ct_host.view(np.int32)).to(dev)
     out = torch.zeros((len(nl.outputs), n + 1), dtype=torch.int32, device=dev)
@@ -378,10 +399,7 @@ def main():
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in evs]
     total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = replica_max_ms(total_ms, world, dev)
     ok = verified and np.array_equal(
         arx.client_decrypt(n, kr.s, out.cpu().numpy().view(np.uint32)), truth)
 
@@ -409,7 +427,7 @@ def main():
     achieved = ops / (br_ms / 1e3) / 1e12
     launches_per_step = br_l + ks_l + (1 if len(nl.outputs) else 0)
 
-    value = boots * args.steps * world / (total_ms / 1e3)
+    value = replica_value(boots, args.steps, world, total_ms)
     line = {
         "metric": METRIC, "value": value, "unit": "bootstraps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
