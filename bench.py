@@ -75,7 +75,7 @@ def replica_seed(base: int, rank: int) -> int:
     return base + rank
 
 
-def workload(name: str, gates: int = 64):
+def workload(name: str, gates: int = 64, blocks: int = 8):
     if name == "netlists":
         return I.union([I.ripple_carry_adder(32), I.array_multiplier(8)], name="adder32+mult8"), \
             "32-bit ripple-carry adder + 8x8 array multiplier (plain netlists, one wave per launch)"
@@ -87,6 +87,10 @@ def workload(name: str, gates: int = 64):
         return nl, f"{g} independent 2-input gates (one wave)"
     if name == "dag":
         return I.random_dag(seed=3), "random levelized DAG, 65,536 gates over 40 waves, 5% MUX"
+    if name == "simon":
+        from paper_2306_11006_gb300 import simon as S
+        nl = S.simon_netlist(blocks=blocks)
+        return nl, f"Simon-128/128, {blocks} blocks x 68 rounds (transciphering), one launch per wave"
     if name == "matmul":
         return I.union([I.matmul4x4() for _ in range(8)], name="8x matmul4x4"), \
             "8 simultaneous 4x4 8-bit matrix products (16-bit accumulators), one launch per wave"
@@ -321,11 +325,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="arx", choices=["arx", "reference"])
     ap.add_argument("--workload", default="netlists",
-                    choices=["netlists", "gates", "gates64", "dag", "matmul", "serve", "alu"])
+                    choices=["netlists", "gates", "gates64", "dag", "matmul", "serve", "alu", "simon"])
     ap.add_argument("--clients", type=int, default=4, help="serve: clients (key sets)")
     ap.add_argument("--rate", type=float, default=4.0, help="serve: Poisson arrival rate, requests/s")
     ap.add_argument("--requests", type=int, default=32, help="serve: requests per run")
     ap.add_argument("--gates", type=int, default=64, help="gate count of the independent-gates workload")
+    ap.add_argument("--blocks", type=int, default=8, help="cipher blocks of the simon workload")
     ap.add_argument("--shape", default=None, help="force the blind-rotation launch shape H,GT")
     ap.add_argument("--mode", default="graph", choices=["graph", "plain"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -340,7 +345,7 @@ def main():
             nl, desc = workload("dag")
             return run_reference(args, nl, "serving request mix (oracle on its gate types)")
         return run_serve(args)
-    nl, desc = workload(args.workload, args.gates)
+    nl, desc = workload(args.workload, args.gates, args.blocks)
     if args.impl == "reference":
         return run_reference(args, nl, desc)
 

@@ -185,6 +185,48 @@ def test_small_netlists_bit_exact_in_full(O, keys630, gpu630):
         assert np.array_equal(arx.client_decrypt(630, keys630.s, out), nl.plain_eval(bits))
 
 
+def test_blif_netlists_bit_exact_in_full(O, keys630, gpu630):
+    from paper_2306_11006_gb300 import blif
+    # a Yosys-cell netlist (4-bit adder carry chain with MUX / ANDNOT cells) and a
+    # round trip of a generated comparator through BLIF text
+    cells = [".model add4", ".inputs " + " ".join(f"a{k} b{k}" for k in range(4)) + " c",
+             ".outputs " + " ".join(f"s{k}" for k in range(4)) + " co"]
+    carry = "c"
+    for k in range(4):
+        cells += [f".subckt $_XOR_ A=a{k} B=b{k} Y=p{k}", f".subckt $_XOR_ A=p{k} B={carry} Y=s{k}",
+                  f".subckt $_MUX_ A=a{k} B={carry} S=p{k} Y=c{k}"]
+        carry = f"c{k}"
+    cells += [f".subckt $_ANDNOT_ A={carry} B=b3 Y=t", ".subckt $_ORNOT_ A=t B=b3 Y=co", ".end"]
+    for nl in (blif.read_blif("\n".join(cells)), blif.read_blif(blif.write_blif(I.comparator(3)))):
+        bits, ct = _encrypt_inputs(O, keys630, nl, 97)
+        out = np.zeros((len(nl.outputs), 631), np.uint32)
+        arx.eval_netlist(nl, ct, out)
+        assert np.array_equal(out, keys630.ctx.eval_netlist(nl, ct)), nl.name
+        assert np.array_equal(arx.client_decrypt(630, keys630.s, out), nl.plain_eval(bits))
+
+
+def test_simon_rounds_transciphering(O, keys630, gpu630):
+    from paper_2306_11006_gb300 import simon as S
+    rng = np.random.default_rng(11)
+    key = tuple(int(v) for v in rng.integers(0, 2**63, 2, dtype=np.uint64))
+    blocks = [tuple(int(v) for v in rng.integers(0, 2**63, 2, dtype=np.uint64)) for _ in range(2)]
+    # one round: every gate against the oracle
+    nl1 = S.simon_netlist(rounds=1, blocks=1)
+    ct1 = keys630.encrypt(O, I, S.netlist_inputs(blocks[:1], key, 1), 131)
+    out1 = np.zeros((len(nl1.outputs), 631), np.uint32)
+    arx.eval_netlist(nl1, ct1, out1)
+    assert np.array_equal(out1, keys630.ctx.eval_netlist(nl1, ct1))
+    # six rounds on two blocks as one netlist: the decrypted words are the cipher's
+    rounds = 6
+    nl = S.simon_netlist(rounds=rounds, blocks=2)
+    ct = keys630.encrypt(O, I, S.netlist_inputs(blocks, key, rounds), 132)
+    out = np.zeros((len(nl.outputs), 631), np.uint32)
+    with arx.Plan(nl, mode=arx.MODE_GRAPH) as p:
+        p.run(ct, out)
+    dec = arx.client_decrypt(630, keys630.s, out)
+    assert S.netlist_outputs(dec) == [S.encrypt(b, key, rounds) for b in blocks]
+
+
 def test_graph_mode_equals_plain_mode(O, keys630, gpu630):
     nl = I.union([I.ripple_carry_adder(5), I.comparator(4)])
     bits, ct = _encrypt_inputs(O, keys630, nl, 95)
