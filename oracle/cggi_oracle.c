@@ -197,10 +197,11 @@ uint32_t orc_modswitch(uint32_t x) {
   return rounded >> 21;
 }
 
-/* Signed gadget decomposition, Bg = 2^7, l = 3: round x to its top 21 bits and */
-/* write that as sum_p d_p 2^(32-7p) with d_p in [-64, 64), p = 1 first.        */
+/* Signed gadget decomposition (Bg = 2^7, l = 3 by default): round x to its top */
+/* l log2(Bg) bits (21) and write that as sum_p d_p 2^(32 - p log2 Bg) with     */
+/* d_p in [-Bg/2, Bg/2), p = 1 first.                                           */
 void orc_decompose(uint32_t x, int32_t digits[ORC_L]) {
-  const int total = ORC_BG_BITS * ORC_L; /* 21 */
+  const int total = ORC_BG_BITS * ORC_L; /* 21 (20 for l = 2, Bg = 2^10) */
   uint32_t offset = 0;
   for (int p = 1; p <= ORC_L; p++) offset += (1u << (ORC_BG_BITS - 1)) << (32 - ORC_BG_BITS * p);
   uint32_t y = x + (1u << (32 - total - 1)) + offset;

@@ -19,7 +19,10 @@
  *
  * Parameters: N = 1024, k = 1, Bg = 2^7, l = 3, key-switch base 2^2 with t = 8,
  * Torus32 = uint32 mod 2^32.  The LWE dimension n is a runtime argument
- * (1 <= n <= 1024; the standard set uses 630, Sec. 2.2).
+ * (1 <= n <= 1024; the standard set uses 630, Sec. 2.2).  Building with
+ * -DORC_L=2 -DORC_BG_BITS=10 gives the variant with l = 2 (the paper's Fig. 2
+ * draws 4 forward DFTs, i.e. (k+1) l = 4) and Bg = 2^10; the arrays documented
+ * with 6 rows then have 2 l = 4.
  *
  * Parity status: every function here is pinned by a CPU test (closed forms,
  * brute force, special cases); none is "parity unpinned".
@@ -34,9 +37,11 @@ extern "C" {
 #endif
 
 #define ORC_N 1024          /* TLWE ring degree (Sec. 2.2: "1024-degree polynomials") */
+#ifndef ORC_L               /* the default set; a second build takes l = 2, Bg = 2^10 */
 #define ORC_BG_BITS 7       /* gadget base Bg = 2^7 */
 #define ORC_L 3             /* gadget length l */
-#define ORC_ROWS 6          /* (k+1) l rows of a TGSW sample */
+#endif
+#define ORC_ROWS (2 * ORC_L) /* (k+1) l rows of a TGSW sample */
 #define ORC_KS_BITS 2       /* key-switch base 2^2 */
 #define ORC_KS_T 8          /* key-switch digits */
 #define ORC_MU 0x20000000u  /* encoding of "true": +1/8 of the torus */

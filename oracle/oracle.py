@@ -17,6 +17,9 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "cggi_oracle.c")
 LIB = os.path.join(HERE, "liboracle.so")
+# the gadget variants: l -> (library, compile-time definitions)
+VARIANTS = {3: (LIB, []), 2: (os.path.join(HERE, "liboracle_l2.so"), ["-DORC_L=2", "-DORC_BG_BITS=10"])}
+BG_BITS = {3: 7, 2: 10}
 
 N = 1024
 L = 3
@@ -27,7 +30,7 @@ MU = 1 << 29
 AND, NAND, OR, NOR, XOR, XNOR, NOT, MUX, COPY, CONST0, CONST1 = range(11)
 
 _lock = threading.Lock()
-_lib = None
+_libs = {}
 
 _u32p = np.ctypeslib.ndpointer(np.uint32, flags="C_CONTIGUOUS")
 _i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
@@ -37,24 +40,25 @@ _u8p = np.ctypeslib.ndpointer(np.uint8, flags="C_CONTIGUOUS")
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle into oracle/liboracle.so with gcc (plain -O2)."""
-    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(
-        os.path.getmtime(SRC), os.path.getmtime(os.path.join(HERE, "cggi_oracle.h"))
-    ):
-        tmp = LIB + f".{os.getpid()}.tmp"
-        subprocess.check_call(
-            ["gcc", "-O2", "-std=gnu11", "-shared", "-fPIC", "-o", tmp, SRC, "-lpthread"]
-        )
-        os.replace(tmp, LIB)
+    """Compile the oracle with gcc (plain -O2): oracle/liboracle.so (l = 3,
+    Bg = 2^7) and oracle/liboracle_l2.so (l = 2, Bg = 2^10)."""
+    deps = max(os.path.getmtime(SRC), os.path.getmtime(os.path.join(HERE, "cggi_oracle.h")))
+    for path, defs in VARIANTS.values():
+        if force or not os.path.exists(path) or os.path.getmtime(path) < deps:
+            tmp = path + f".{os.getpid()}.tmp"
+            subprocess.check_call(["gcc", "-O2", "-std=gnu11", *defs, "-shared", "-fPIC", "-o", tmp, SRC, "-lpthread"])
+            os.replace(tmp, path)
     return LIB
 
 
-def lib():
-    global _lib
+def lib(l: int = L):
+    """The oracle library of gadget length l (3: Bg = 2^7; 2: Bg = 2^10)."""
     with _lock:
-        if _lib is None:
+        if l not in _libs:
+            if l not in VARIANTS:
+                raise ValueError(f"no oracle variant with l = {l}")
             build()
-            h = ctypes.CDLL(LIB)
+            h = ctypes.CDLL(VARIANTS[l][0])
             sig = {
                 "orc_gl_mul": (ctypes.c_uint64, [ctypes.c_uint64, ctypes.c_uint64]),
                 "orc_gl_pow": (ctypes.c_uint64, [ctypes.c_uint64, ctypes.c_uint64]),
@@ -84,8 +88,8 @@ def lib():
                 f = getattr(h, name)
                 f.restype = res
                 f.argtypes = args
-            _lib = h
-    return _lib
+            _libs[l] = h
+    return _libs[l]
 
 
 def _u32(x):
@@ -119,9 +123,9 @@ def modswitch(x: int) -> int:
     return lib().orc_modswitch(x)
 
 
-def decompose(x: int):
-    d = np.zeros(L, np.int32)
-    lib().orc_decompose(x, d)
+def decompose(x: int, l: int = L):
+    d = np.zeros(l, np.int32)
+    lib(l).orc_decompose(x, d)
     return d
 
 
@@ -132,11 +136,13 @@ def ks_digits(x: int):
 
 
 def keygen(kr):
-    """kr: inputs.KeyRandomness -> (bsk [n][6][2][N] u32, ksk [N][8][4][n+1] u32)."""
+    """kr: inputs.KeyRandomness -> (bsk [n][2l][2][N] u32, ksk [N][8][4][n+1] u32);
+    the gadget length l follows the rows of kr.bsk_mask."""
     n = kr.n
-    bsk = np.zeros((n, ROWS, 2, N), np.uint32)
+    rows = kr.bsk_mask.shape[1]
+    bsk = np.zeros((n, rows, 2, N), np.uint32)
     ksk = np.zeros((N, KS_T, 4, n + 1), np.uint32)
-    lib().orc_keygen(n, kr.s, kr.K, kr.bsk_mask, kr.bsk_noise, kr.ksk_mask, kr.ksk_noise, bsk, ksk)
+    lib(rows // 2).orc_keygen(n, kr.s, kr.K, kr.bsk_mask, kr.bsk_noise, kr.ksk_mask, kr.ksk_noise, bsk, ksk)
     return bsk, ksk
 
 
@@ -174,32 +180,34 @@ class Context:
         self.n = n
         self._bsk = _u32(bsk)
         self._ksk = _u32(ksk)
-        self.h = lib().orc_ctx_create(n, self._bsk, self._ksk)
+        self.l = self._bsk.size // (n * 2 * 2 * N)  # bsk is [n][2l][2][N]
+        self.h = lib(self.l).orc_ctx_create(n, self._bsk, self._ksk)
 
     def __del__(self):
-        if getattr(self, "h", None) and _lib is not None:
-            _lib.orc_ctx_destroy(self.h)
+        h = _libs.get(getattr(self, "l", None))
+        if getattr(self, "h", None) and h is not None:
+            h.orc_ctx_destroy(self.h)
             self.h = None
 
     def external_product(self, i, t0, t1):
         o0 = np.zeros(N, np.uint32)
         o1 = np.zeros(N, np.uint32)
-        lib().orc_external_product(self.h, i, _u32(t0), _u32(t1), o0, o1)
+        lib(self.l).orc_external_product(self.h, i, _u32(t0), _u32(t1), o0, o1)
         return o0, o1
 
     def blind_rotate(self, abar, bbar):
         acc = np.zeros(2 * N, np.uint32)
-        lib().orc_blind_rotate(self.h, _u32(abar), int(bbar), acc)
+        lib(self.l).orc_blind_rotate(self.h, _u32(abar), int(bbar), acc)
         return acc.reshape(2, N)
 
     def keyswitch(self, lwe_N):
         out = np.zeros(self.n + 1, np.uint32)
-        lib().orc_keyswitch(self.h, _u32(lwe_N), out)
+        lib(self.l).orc_keyswitch(self.h, _u32(lwe_N), out)
         return out
 
     def bootstrap_to_N(self, ct):
         out = np.zeros(N + 1, np.uint32)
-        lib().orc_bootstrap_to_N(self.h, _u32(ct), out)
+        lib(self.l).orc_bootstrap_to_N(self.h, _u32(ct), out)
         return out
 
     def gates(self, types, a, b=None, c=None, nthreads=None):
@@ -208,13 +216,13 @@ class Context:
         b = a if b is None else _u32(b).reshape(-1, self.n + 1)
         c = a if c is None else _u32(c).reshape(-1, self.n + 1)
         out = np.zeros_like(a)
-        lib().orc_gates(self.h, types, a, b, c, out, len(types), nthreads or os.cpu_count() or 1)
+        lib(self.l).orc_gates(self.h, types, a, b, c, out, len(types), nthreads or os.cpu_count() or 1)
         return out
 
     def eval_netlist(self, nl, ct_in, nthreads=None):
         ct_in = _u32(ct_in).reshape(-1, self.n + 1)
         out = np.zeros((len(nl.outputs), self.n + 1), np.uint32)
-        rc = lib().orc_eval_netlist(
+        rc = lib(self.l).orc_eval_netlist(
             self.h, nl.num_inputs, nl.num_gates, nl.type, nl.in0, nl.in1, nl.in2,
             len(nl.outputs), nl.outputs, ct_in, out, nthreads or os.cpu_count() or 1,
         )

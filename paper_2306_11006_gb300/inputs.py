@@ -53,18 +53,20 @@ class KeyRandomness:
 
 
 def key_randomness(seed: int, n: int = LWE_N, noiseless: bool = False,
-                   trivial_bsk: bool = False) -> KeyRandomness:
+                   trivial_bsk: bool = False, l: int = 3) -> KeyRandomness:
     """Key randomness from one seed.
 
     noiseless: all noise terms zero (masks still uniform).
     trivial_bsk: additionally zero the bootstrapping-key masks (a noiseless,
     trivial TGSW encryption), used by closed-form checks of blind rotation.
+    l: gadget length (3 rows per key component by default; 2 for the variant).
     """
+    rows = 2 * l
     rng = _rng(seed)
     s = rng.integers(0, 2, n, dtype=np.uint8)
     K = rng.integers(0, 2, N, dtype=np.uint8)
-    bsk_mask = rng.integers(0, 2 ** 32, (n, ROWS, N), dtype=np.uint32)
-    bsk_noise = torus_noise(rng, SIGMA_TRLWE, (n, ROWS, N))
+    bsk_mask = rng.integers(0, 2 ** 32, (n, rows, N), dtype=np.uint32)
+    bsk_noise = torus_noise(rng, SIGMA_TRLWE, (n, rows, N))
     ksk_mask = rng.integers(0, 2 ** 32, (N, KS_T, 3, n), dtype=np.uint32)
     ksk_noise = torus_noise(rng, SIGMA_LWE, (N, KS_T, 3))
     if noiseless or trivial_bsk:

@@ -48,3 +48,9 @@ def keys630(O, I):
 @pytest.fixture(scope="session")
 def keys64(O, I):
     return Keys(O, I, 5, 64)
+
+
+@pytest.fixture(scope="session")
+def keys512_l2(O, I):
+    """The paper's own parameter set: n = 512, gadget l = 2 (Bg = 2^10)."""
+    return Keys(O, I, 7, 512, l=2)
