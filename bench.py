@@ -43,9 +43,15 @@ from paper_2306_11006_gb300 import inputs as I  # noqa: E402
 METRIC = "gate bootstraps/sec on 1 GB300 (bit-exact vs oracle); netlist p50/p99 latency ms"
 LWE_N = 630
 # blind rotation work per bootstrap in 32-bit modular multiply-accumulates (two CRT
-# primes): per CMux, 8 length-1024 transforms x 5120 butterflies + 2 x 6 x 1024 MACs,
-# each once per prime.
-MODMUL_PER_CMUX = 2 * (8 * 5120 + 12 * 1024)
+# primes): per CMux, (2l + 2) length-1024 transforms x 5120 butterflies + 2 x 2l x 1024
+# MACs, each once per prime (l = 3: 8 transforms, 12 MAC rows).
+
+
+def modmul_per_cmux(l: int = 3) -> int:
+    return 2 * ((2 * l + 2) * 5120 + 2 * 2 * l * 1024)
+
+
+MODMUL_PER_CMUX = modmul_per_cmux(3)
 # integer-ALU peak: 152 SMs x 2070 MHz x 64 IMAD lanes/clk / 3 IMADs per Shoup or
 # Montgomery modular multiply (derivation in the design doc)
 ALU_PEAK_TMODMUL = 152 * 2.070e9 * 64 / 3 / 1e12
@@ -142,13 +148,12 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def cpu_baseline(nl, budget_s: float = 20.0):
+def cpu_baseline(nl, budget_s: float = 20.0, n: int = LWE_N, l: int = 3):
     """The plain C oracle on this host's cores, on a bounded sample of the workload's
     bootstrapped gates (random inputs), in bootstraps per second."""
     from oracle import oracle as O
 
-    n = LWE_N
-    kr = I.key_randomness(0, n)
+    kr = I.key_randomness(0, n, l=l)
     bsk, ksk = O.keygen(kr)
     ctx = O.Context(n, bsk, ksk)
     cores = os.cpu_count() or 1
@@ -174,18 +179,19 @@ def cpu_baseline(nl, budget_s: float = 20.0):
 
 
 def run_reference(args, nl, desc):
+    n, l = (512, 2) if args.paper_params else (LWE_N, 3)
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     for _ in range(args.warmup):
-        cpu_baseline(nl, budget_s=2.0)
-    vals = [cpu_baseline(nl, budget_s=max(4.0, 60.0 / max(args.steps, 1))) for _ in range(args.steps)]
+        cpu_baseline(nl, budget_s=2.0, n=n, l=l)
+    vals = [cpu_baseline(nl, budget_s=max(4.0, 60.0 / max(args.steps, 1)), n=n, l=l) for _ in range(args.steps)]
     v = statistics.mean(x["value"] for x in vals)
     boots = sum(I.BOOTSTRAPS[int(t)] for t in nl.type)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "bootstraps/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * boots / v,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-            "data": "synthetic", "config": {"workload": desc, "lwe_n": LWE_N},
+            "data": "synthetic", "config": {"workload": desc, "lwe_n": n, "gadget": f"l={l}"},
             "cpu_baseline": {"kind": "oracle", "cores": vals[0]["cores"], "sample": vals[0]["sample"], "value": v},
             "e2e": {"value": v, "unit": "bootstraps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -334,6 +340,8 @@ def main():
     ap.add_argument("--shape", default=None, help="force the blind-rotation launch shape H,GT")
     ap.add_argument("--mode", default="graph", choices=["graph", "plain"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--paper-params", action="store_true",
+                    help="the paper's own set: n = 512, gadget l = 2 (Bg = 2^10), instead of n = 630, l = 3")
     args = ap.parse_args()
     if args.workload == "alu":
         if args.impl == "reference":
@@ -364,10 +372,10 @@ def main():
     stream = torch.cuda.current_stream(dev)
 
     # keys and inputs: client-side key generation and encryption from seeded randomness
-    n = LWE_N
-    kr = I.key_randomness(0, n)
+    n, l = (512, 2) if args.paper_params else (LWE_N, 3)
+    kr = I.key_randomness(0, n, l=l)
     bsk, ksk = arx.client_keygen(kr)
-    keyset = arx.load_keys(bsk, ksk, n)
+    keyset = arx.load_keys(bsk, ksk, n, l=l)
     bits = I.random_bits(replica_seed(1000, rank), nl.num_inputs)
     m, e = I.encryption_randomness(replica_seed(2000, rank), nl.num_inputs, n)
     ct_host = arx.client_encrypt(n, kr.s, m, e, bits)
@@ -425,10 +433,11 @@ def main():
     waves_of = {}
     for H, GT, jobs in plan.shapes():
         if jobs:
-            k = {12: "br_cluster_kernel", 24: "br_cluster4_kernel", 48: "br_cluster8_kernel"}.get(H, f"br_kernel<{H},{GT}>")
+            k = {12: "br_cluster_kernel", 24: "br_cluster4_kernel", 48: "br_cluster8_kernel",
+                 40: "br_cluster8_kernel<L=2>"}.get(H, f"br_kernel<{H},{GT}>")
             waves_of[k] = waves_of.get(k, 0) + 1
     br_kernels = sorted(waves_of, key=lambda k: -waves_of[k])  # dominant (most waves) first
-    ops = boots * n * MODMUL_PER_CMUX
+    ops = boots * n * modmul_per_cmux(l)
     achieved = ops / (br_ms / 1e3) / 1e12
     launches_per_step = br_l + ks_l + (1 if len(nl.outputs) else 0)
 
@@ -437,7 +446,7 @@ def main():
         "metric": METRIC, "value": value, "unit": "bootstraps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": desc, "lwe_n": n, "N": 1024, "mode": args.mode, "shape": args.shape, "gates": nl.num_gates,
+        "config": {"workload": desc, "lwe_n": n, "N": 1024, "gadget": f"l={l}, Bg=2^{arx.GADGET_BITS[l]}", "mode": args.mode, "shape": args.shape, "gates": nl.num_gates,
                    "bootstraps_per_step": boots, "waves": plan.waves,
                    "l2": "flushed between steps (256 MiB write)", "parallelism": "replicas" if world > 1 else "1 GPU"},
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
@@ -460,7 +469,7 @@ def main():
     plan.close()
     arx.unload_keys(keyset)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(nl)
+        line["cpu_baseline"] = cpu_baseline(nl, n=n, l=l)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -85,6 +85,16 @@ int arx_load_keys(const uint32_t *bsk, const uint32_t *ksk);
 /* As arx_load_keys for LWE dimension lwe_n (1..630); stream may be NULL. */
 int arx_load_keys_ex(const uint32_t *bsk, const uint32_t *ksk, int lwe_n, void *stream);
 
+/* As arx_load_keys_ex with the gadget given: (l, bg_bits) = (3, 7), the default
+ * set, or (2, 10), the gadget of the paper's own experiments (Fig. 2 draws 4
+ * forward DFTs per CMux, (k+1) l = 4; Sec. 6 uses n = 512).  The bootstrapping
+ * key then has 2 l rows per index: [n][2l][2][N], row r = c*l + (p-1), gadget
+ * level p scaled by 2^(32 - p bg_bits).  Key sets with l = 2 run their blind
+ * rotations on one kernel of their own (the eight-CTA cluster kernel built for
+ * 10-bit digits) whatever the launch-shape override.  ARX_EINVAL for any other
+ * gadget. */
+int arx_load_keys_gadget(const uint32_t *bsk, const uint32_t *ksk, int lwe_n, int l, int bg_bits, void *stream);
+
 /* Free a key set.  ARX_EBUSY while a plan references it. */
 int arx_unload_keys(int keyset);
 
@@ -267,6 +277,11 @@ int arx_probe_alu(double *rate, int count);
 int arx_client_keygen(int lwe_n, const uint8_t *s, const uint8_t *K, const uint32_t *bsk_mask,
                       const int32_t *bsk_noise, const uint32_t *ksk_mask, const int32_t *ksk_noise,
                       uint32_t *bsk, uint32_t *ksk);
+/* As arx_client_keygen with the gadget (l, bg_bits) = (3, 7) or (2, 10) (see
+ * arx_load_keys_gadget): bsk_mask / bsk_noise are [n][2l][N], bsk [n][2l][2][N]. */
+int arx_client_keygen_gadget(int lwe_n, int l, int bg_bits, const uint8_t *s, const uint8_t *K,
+                             const uint32_t *bsk_mask, const int32_t *bsk_noise, const uint32_t *ksk_mask,
+                             const int32_t *ksk_noise, uint32_t *bsk, uint32_t *ksk);
 /* ct[g] = (mask[g], <mask[g], s> + noise[g] + (bits[g] ? +1/8 : -1/8)). */
 int arx_client_encrypt(int lwe_n, const uint8_t *s, const uint32_t *mask, const int32_t *noise,
                        const uint8_t *bits, size_t count, uint32_t *ct);

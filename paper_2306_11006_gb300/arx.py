@@ -44,6 +44,7 @@ _NLP = ctypes.POINTER(Netlist_C)
 SIGNATURES = {
     "arx_load_keys": (_i, [_vp, _vp]),
     "arx_load_keys_ex": (_i, [_vp, _vp, _i, _vp]),
+    "arx_load_keys_gadget": (_i, [_vp, _vp, _i, _i, _i, _vp]),
     "arx_unload_keys": (_i, [_i]),
     "arx_use_keys": (_i, [_i]),
     "arx_keyset_bytes": (_sz, [_i]),
@@ -73,6 +74,7 @@ SIGNATURES = {
     "arx_device_sms": (_i, []),
     "arx_probe_alu": (_i, [_vp, _i]),
     "arx_client_keygen": (_i, [_i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "arx_client_keygen_gadget": (_i, [_i, _i, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "arx_client_encrypt": (_i, [_i, _vp, _vp, _vp, _vp, _sz, _vp]),
     "arx_client_decrypt": (_i, [_i, _vp, _vp, _sz, _vp]),
 }
@@ -136,8 +138,15 @@ def _host_u8(x):
 
 
 # ------------------------------------------------------------------- keys ---
-def load_keys(bsk, ksk, lwe_n: int = LWE_N, stream=None) -> int:
-    return _check(lib().arx_load_keys_ex(_ptr(bsk), _ptr(ksk), lwe_n, _stream(stream)))
+GADGET_BITS = {3: 7, 2: 10}  # gadget length l -> log2 Bg
+
+
+def load_keys(bsk, ksk, lwe_n: int = LWE_N, stream=None, l: int = 3) -> int:
+    """Load a key pair; l = 2 selects the gadget Bg = 2^10 (bsk [n][4][2][N])."""
+    if l == 3:
+        return _check(lib().arx_load_keys_ex(_ptr(bsk), _ptr(ksk), lwe_n, _stream(stream)))
+    return _check(lib().arx_load_keys_gadget(_ptr(bsk), _ptr(ksk), lwe_n, l, GADGET_BITS.get(l, 0),
+                                             _stream(stream)))
 
 
 def unload_keys(keyset: int) -> None:
@@ -326,12 +335,16 @@ def probe_alu() -> dict:
 
 # ------------------------------------------------------------ client side ---
 def client_keygen(kr):
-    """Key pair from an inputs.KeyRandomness: (bsk [n][6][2][N], ksk [N][8][4][n+1])."""
+    """Key pair from an inputs.KeyRandomness: (bsk [n][2l][2][N], ksk [N][8][4][n+1]);
+    the gadget length l follows the rows of kr.bsk_mask (6: l = 3, 4: l = 2)."""
     n = kr.n
-    bsk = np.zeros((n, 6, 2, N), np.uint32)
+    rows = kr.bsk_mask.shape[1]
+    bsk = np.zeros((n, rows, 2, N), np.uint32)
     ksk = np.zeros((N, 8, 4, n + 1), np.uint32)
     arrs = [np.ascontiguousarray(a) for a in (kr.s, kr.K, kr.bsk_mask, kr.bsk_noise, kr.ksk_mask, kr.ksk_noise)]
-    _check(lib().arx_client_keygen(n, *[_ptr(a) for a in arrs], _ptr(bsk), _ptr(ksk)))
+    l = rows // 2
+    _check(lib().arx_client_keygen_gadget(n, l, GADGET_BITS.get(l, 0), *[_ptr(a) for a in arrs], _ptr(bsk),
+                                          _ptr(ksk)))
     return bsk, ksk
 
 

@@ -29,6 +29,8 @@ struct TwiddleConst {
   uint2 inv1[2][32];      // inverse pass 1: index (h - 1) + j, h = 1, 2, 4, 8, 16, j < h
   uint32_t dig_c[2];      // (-64 - 64 zeta[1]) mod q: first-stage offset for raw digits
   uint32_t dig_d[2];      // (64 zeta[1] - 64) mod q
+  uint32_t dig_c2[2];     // the same for 10-bit digits (gadget l = 2, Bg = 2^10): (-512 - 512 zeta[1]) mod q
+  uint32_t dig_d2[2];     // (512 zeta[1] - 512) mod q
   uint2 psi512[2];        // psi^-512 and psi^-256 (last stages of the split inverse)
   uint2 psi256[2];
 };
@@ -99,7 +101,8 @@ struct BrShape {
 // Twiddle tables for the two CRT primes (computed on the host, once).
 void make_twiddles(TwiddleConst *tc, TwiddleGlobal *tg);
 
-cudaError_t launch_bsk_to_ntt(const uint32_t *bsk_coef, int n, uint32_t *bsk_ntt, const TwiddleConst &tc,
+// rows = (k+1) l TGSW rows per key index (6, or 4 for the gadget l = 2)
+cudaError_t launch_bsk_to_ntt(const uint32_t *bsk_coef, int n, int rows, uint32_t *bsk_ntt, const TwiddleConst &tc,
                               const TwiddleGlobal *tg, cudaStream_t st);
 size_t br_smem(BrShape s);
 int br_threads(BrShape s);
@@ -128,7 +131,15 @@ constexpr int kCluster8H = 48;
 size_t br_cluster8_smem();
 cudaError_t launch_br_cluster8(const BrArgs &args, int clusters, cudaStream_t st);
 int br_cluster8_occupancy();
-inline bool is_cluster_shape(BrShape s) { return s.H == kClusterH || s.H == kCluster4H || s.H == kCluster8H; }
+// Shape {kCluster8L2H, 1}: the eight-CTA kernel for key sets with gadget l = 2
+// (Bg = 2^10); chosen automatically for such key sets, never by an override.
+constexpr int kCluster8L2H = 40;
+size_t br_cluster8_l2_smem();
+cudaError_t launch_br_cluster8_l2(const BrArgs &args, int clusters, cudaStream_t st);
+int br_cluster8_l2_occupancy();
+inline bool is_cluster_shape(BrShape s) {
+  return s.H == kClusterH || s.H == kCluster4H || s.H == kCluster8H || s.H == kCluster8L2H;
+}
 
 // per-shape launchers (one translation unit per H)
 cudaError_t launch_br_h1(const BrArgs &args, int GT, int grid, cudaStream_t st);

@@ -18,7 +18,9 @@
 // update identical copies of ACC_h.  Every cross-CTA dependency is a transaction
 // count on an mbarrier (double-buffered by CMux parity); every wait is bounded.
 // With nine warps per CTA the loop-invariant per-lane twiddles of each warp stay
-// in registers.
+// in registers.  The kernel is a template on the gadget length L: 3 (Bg = 2^7,
+// 7-bit digits, six forward warps) or 2 (Bg = 2^10, 10-bit digits, four forward
+// warps and the TGSW rows 2h, 2h+1 of the paper's own parameter set).
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -30,29 +32,32 @@ namespace brc8 {
 
 using namespace clu;
 
-constexpr int kFwd = 6;                     // forward warps: (row 0..2) x (prime 0..1)
-constexpr int kCons = 8;                    // + 2 warps for the digits and the CRT pass
+constexpr int kCons = 8;                    // forward warps + helpers for the digits and the CRT pass
 constexpr int kThreads = (kCons + 1) * 32;  // + producer warp
 constexpr int kConsThreads = kCons * 32;    // 256
-constexpr int kStages = 6;                  // ring of 16 KiB key rows: two CMux ahead
+constexpr int kStages = 6;                  // ring of 16 KiB key rows: two CMux ahead (L = 3)
 constexpr int kAbarPitch = 640;
 constexpr int kQuarter = 256;
-constexpr uint32_t kPeerBytes = kFwd * kQuarter * 4;          // the peer's six product quarters
 constexpr uint32_t kPartnerBytes = 3 * 2 * kQuarter * 4;      // three partners x two primes
 
-// shared memory (bytes)
-constexpr size_t kRingBytes = (size_t)kStages * kChunkBytes;
-constexpr size_t kAccBytes = kN * 4;                  // ACC_h
-constexpr size_t kDigBytes = 3 * 256 * 4;             // [row][k] digit bytes of k, k+256, k+512, k+768
-constexpr size_t kOwnBytes = 2 * 3 * kQuarter * 4;    // [prime][row][quarter Q] products for output h
-constexpr size_t kOthBytes = 2 * 2 * 3 * kQuarter * 4;  // [parity][prime][row][quarter Q] for output 1-h
-constexpr size_t kSlotBytes = 2 * 2 * kQuarter * 4;   // [parity][prime][quarter Q] the peer's row sums
-constexpr size_t kPostBytes = 2 * 2 * 4 * kQuarter * 4;  // [parity][prime][quarter][k] inverse quarters
-constexpr size_t kScrBytes = (size_t)kFwd * kQuarter * 4;
-constexpr size_t kAbarBytes = kAbarPitch * 2;
-constexpr size_t kBarBytes = (2 * kStages + 4) * 8 + 16;
-constexpr size_t kSmem = kRingBytes + kAccBytes + kDigBytes + kOwnBytes + kOthBytes + kSlotBytes + kPostBytes +
-                         kScrBytes + kAbarBytes + kBarBytes;
+template <int L>
+struct Cfg {
+  static constexpr int kFwd = 2 * L;                              // forward warps: (row) x (prime)
+  static constexpr uint32_t kPeerBytes = kFwd * kQuarter * 4;     // the peer's product quarters
+  // shared memory (bytes)
+  static constexpr size_t kRingBytes = (size_t)kStages * kChunkBytes;
+  static constexpr size_t kAccBytes = kN * 4;                     // ACC_h
+  static constexpr size_t kDigBytes = (L == 3 ? 3 * 256 : 4 * 256) * 4;  // packed digits (see make_digits*)
+  static constexpr size_t kOwnBytes = 2 * L * kQuarter * 4;       // [prime][row][quarter Q] products for output h
+  static constexpr size_t kOthBytes = 2 * 2 * L * kQuarter * 4;   // [parity][prime][row][quarter Q] for output 1-h
+  static constexpr size_t kSlotBytes = 2 * 2 * kQuarter * 4;      // [parity][prime][quarter Q] the peer's row sums
+  static constexpr size_t kPostBytes = 2 * 2 * 4 * kQuarter * 4;  // [parity][prime][quarter][k] inverse quarters
+  static constexpr size_t kScrBytes = (size_t)kFwd * kQuarter * 4;
+  static constexpr size_t kAbarBytes = kAbarPitch * 2;
+  static constexpr size_t kBarBytes = (2 * kStages + 4) * 8 + 16;
+  static constexpr size_t kSmem = kRingBytes + kAccBytes + kDigBytes + kOwnBytes + kOthBytes + kSlotBytes +
+                                  kPostBytes + kScrBytes + kAbarBytes + kBarBytes;
+};
 
 // Forward quarter transform with its per-lane twiddles in registers (zc: middle
 // pass, lengths 32, 16, 8; zq: last pass, lengths 4, 2, 1; same entries as the
@@ -155,15 +160,18 @@ __device__ __forceinline__ void inv_quarter_r(uint32_t (&x)[8], uint32_t *xbuf, 
   for (int e = 0; e < 8; ++e) x[e] = shoup_mul(zt[e].x, zt[e].y, x[e], pr.q);
 }
 
+template <int L>
 __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(kThreads, 1)
     br_cluster8_kernel(const __grid_constant__ BrArgs args) {
+  using C = Cfg<L>;
+  constexpr int kFwd = C::kFwd;
   extern __shared__ __align__(128) uint8_t smem[];
   uint32_t *ring = reinterpret_cast<uint32_t *>(smem);
-  uint32_t *A = reinterpret_cast<uint32_t *>(smem + kRingBytes);
-  uint32_t *D = A + kN;                          // [row][256]
-  uint32_t *own = D + 3 * 256;                   // [prime][row][256], swizzled (swp)
-  uint32_t *oth = own + 6 * kQuarter;            // [parity][prime][row][256], same layout
-  uint32_t *slots = oth + 12 * kQuarter;         // [parity][prime][256], same layout, zero between uses
+  uint32_t *A = reinterpret_cast<uint32_t *>(smem + C::kRingBytes);
+  uint32_t *D = A + kN;                          // packed digits
+  uint32_t *own = D + C::kDigBytes / 4;          // [prime][row][256], swizzled (swp)
+  uint32_t *oth = own + 2 * L * kQuarter;        // [parity][prime][row][256], same layout
+  uint32_t *slots = oth + 4 * L * kQuarter;      // [parity][prime][256], same layout, zero between uses
   uint32_t *post = slots + 4 * kQuarter;         // [parity][prime][quarter][256], natural order
   uint32_t *scratch = post + 16 * kQuarter;      // [forward warp][256]
   uint16_t *abar = reinterpret_cast<uint16_t *>(scratch + kFwd * kQuarter);
@@ -199,13 +207,13 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(kThreads, 1)
   const int nclusters = gridDim.x / 8, cid = blockIdx.x / 8;
   const int tiles = args.num_jobs;
 
-  if (warp == kCons) {  // producer: stream the three key rows of component h for every CMux
+  if (warp == kCons) {  // producer: stream the L key rows of component h for every CMux
     if (lane == 0 && tiles > 0) {
       uint32_t jc = 0;
       bool ok = true;
       for (int tile = cid; tile < tiles && ok; tile += nclusters) {
         for (int i = 0; i < n && ok; ++i) {
-          for (int rr = 0; rr < 3; ++rr, ++jc) {
+          for (int rr = 0; rr < L; ++rr, ++jc) {
             const uint32_t slot = jc % kStages;
             if (jc >= (uint32_t)kStages &&
                 !mbar_wait(empty + slot, ((jc / kStages) - 1) & 1u, abort_flag, args.status)) {
@@ -213,8 +221,8 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(kThreads, 1)
               break;
             }
             mbar_expect_tx(full + slot, kChunkBytes);
-            bulk_g2s(ring + slot * kChunkWords, args.bsk + ((size_t)i * 6 + 3 * h + rr) * kChunkWords, kChunkBytes,
-                     full + slot);
+            bulk_g2s(ring + slot * kChunkWords, args.bsk + ((size_t)i * 2 * L + L * h + rr) * kChunkWords,
+                     kChunkBytes, full + slot);
           }
         }
       }
@@ -228,9 +236,13 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(kThreads, 1)
     }
   } else if (tiles > 0) {
     const bool fwd = warp < kFwd;
-    const int rr = fwd ? warp >> 1 : 0, P = warp & 1;  // forward warps: row 3h + rr, prime P
+    const int rr = fwd ? warp >> 1 : 0, P = warp & 1;  // forward warps: row L h + rr, prime P
     const int tid = threadIdx.x;                         // 0 .. 255
-    const PrimeRT pr = prime_rt(P, args.tc);
+    PrimeRT pr = prime_rt(P, args.tc);
+    if (L == 2) {  // first-stage offsets of 10-bit digits
+      pr.dc = args.tc.dig_c2[P];
+      pr.dd = args.tc.dig_d2[P];
+    }
     uint32_t *myscr = scratch + (fwd ? warp : 0) * kQuarter;
     const uint2 *tw1f = args.tc.fwd1[P], *tw1i = args.tc.inv1[P];
     const uint2 z1 = args.tc.fwd1[P][1], z23 = args.tc.fwd1[P][2 + (Q >> 1)];
@@ -263,21 +275,27 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(kThreads, 1)
 
       for (int i = 0; i < n; ++i, ++cm) {
         const uint32_t par = cm & 1u, ph = (cm >> 1) & 1u;
-        make_digits4(D, A, abar[i], tid, kConsThreads);
+        if (L == 3)
+          make_digits4(D, A, abar[i], tid, kConsThreads);
+        else
+          make_digits_l2(D, A, abar[i], tid, kConsThreads);
         named_bar(1, kConsThreads);
         if (fwd) {
           uint32_t x[8];
-          load_first2(x, D + rr * 256, z1, z23, Q, pr, lane);
+          if (L == 3)
+            load_first2(x, D + rr * 256, z1, z23, Q, pr, lane);
+          else
+            load_first2_l2(x, D + rr * 512, z1, z23, Q, pr, lane);
           fwd_quarter_r(x, myscr, tw1f, zc, zq, Q, pr, lane);
-          const uint32_t jc = (it * (uint32_t)n + (uint32_t)i) * 3u + (uint32_t)rr;
+          const uint32_t jc = (it * (uint32_t)n + (uint32_t)i) * (uint32_t)L + (uint32_t)rr;
           const uint32_t slot = jc % kStages;
           mbar_wait(full + slot, (jc / kStages) & 1u, abort_flag, args.status);
           // key row layout: position 32 L + E at word ((E >> 2) * 32 + L) * 4 + (E & 3)
           const uint4 *Bown = reinterpret_cast<const uint4 *>(ring + slot * kChunkWords + (h * 2 + P) * kN);
           const uint4 *Both = reinterpret_cast<const uint4 *>(ring + slot * kChunkWords + ((1 - h) * 2 + P) * kN);
-          uint32_t *oq = oth + ((par * 2 + P) * 3 + rr) * kQuarter;
+          uint32_t *oq = oth + ((par * 2 + P) * L + rr) * kQuarter;
           uint4 *oth4 = reinterpret_cast<uint4 *>(oq);
-          uint4 *own4 = reinterpret_cast<uint4 *>(own + (P * 3 + rr) * kQuarter);
+          uint4 *own4 = reinterpret_cast<uint4 *>(own + (P * L + rr) * kQuarter);
           // products for the peer's output first: added into its slot while the rest runs
 #pragma unroll
           for (int c = 0; c < 2; ++c) {
@@ -300,20 +318,20 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(kThreads, 1)
           }
           __syncwarp();
           if (lane == 0) mbar_arrive_cta(empty + slot);
-          named_bar(2 + P, 96);  // the three rows of output h, prime P, quarter Q, in place
+          named_bar(2 + P, 32 * L);  // the L rows of output h, prime P, quarter Q, in place
           if (warp == 0 && lane == 0) {
-            mbar_expect_tx(done1 + par, kPeerBytes);
+            mbar_expect_tx(done1 + par, C::kPeerBytes);
             mbar_expect_tx(done2 + par, kPartnerBytes);
           }
           if (rr == 0) {
-            // quarter Q of output h in prime P: three local rows and the peer's sum
+            // quarter Q of output h in prime P: L local rows and the peer's sum
             mbar_wait(done1 + par, ph, abort_flag, args.status);
             uint32_t y[8];
 #pragma unroll
             for (int e = 0; e < 8; ++e) y[e] = 0u;
 #pragma unroll
-            for (int r4 = 0; r4 < 4; ++r4) {
-              uint4 *sl = reinterpret_cast<uint4 *>(r4 < 3 ? own + (P * 3 + r4) * kQuarter : slots + (par * 2 + P) * kQuarter);
+            for (int r4 = 0; r4 <= L; ++r4) {
+              uint4 *sl = reinterpret_cast<uint4 *>(r4 < L ? own + (P * L + r4) * kQuarter : slots + (par * 2 + P) * kQuarter);
 #pragma unroll
               for (int c = 0; c < 2; ++c) {
                 const int ci = swp(8 * lane + 4 * c) >> 2;
@@ -322,7 +340,7 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(kThreads, 1)
                 y[4 * c + 1] += q.y;
                 y[4 * c + 2] += q.z;
                 y[4 * c + 3] += q.w;
-                if (r4 == 3) sl[ci] = make_uint4(0u, 0u, 0u, 0u);  // the slot starts its next use at zero
+                if (r4 == L) sl[ci] = make_uint4(0u, 0u, 0u, 0u);  // the slot starts its next use at zero
               }
             }
             fence_proxy_async_smem();  // the zeroes precede the peer's next bulk additions
@@ -367,30 +385,31 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(kThreads, 1)
 
 }  // namespace brc8
 
-size_t br_cluster8_smem() { return brc8::kSmem; }
-
-cudaError_t launch_br_cluster8(const BrArgs &args, int clusters, cudaStream_t st) {
+namespace {
+template <int L>
+cudaError_t launch8(const BrArgs &args, int clusters, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(brc8::br_cluster8_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)brc8::kSmem);
+    cudaError_t e = cudaFuncSetAttribute(brc8::br_cluster8_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)brc8::Cfg<L>::kSmem);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  brc8::br_cluster8_kernel<<<8 * clusters, brc8::kThreads, brc8::kSmem, st>>>(args);
+  brc8::br_cluster8_kernel<L><<<8 * clusters, brc8::kThreads, brc8::Cfg<L>::kSmem, st>>>(args);
   return cudaGetLastError();
 }
 
-int br_cluster8_occupancy() {
-  if (cudaFuncSetAttribute(brc8::br_cluster8_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)brc8::kSmem) != cudaSuccess) {
+template <int L>
+int occupancy8() {
+  if (cudaFuncSetAttribute(brc8::br_cluster8_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)brc8::Cfg<L>::kSmem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(8, 1, 1);
   cfg.blockDim = dim3(brc8::kThreads, 1, 1);
-  cfg.dynamicSmemBytes = brc8::kSmem;
+  cfg.dynamicSmemBytes = brc8::Cfg<L>::kSmem;
   cudaLaunchAttribute at;
   at.id = cudaLaunchAttributeClusterDimension;
   at.val.clusterDim.x = 8;
@@ -399,11 +418,21 @@ int br_cluster8_occupancy() {
   cfg.attrs = &at;
   cfg.numAttrs = 1;
   int clusters = 0;
-  if (cudaOccupancyMaxActiveClusters(&clusters, brc8::br_cluster8_kernel, &cfg) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveClusters(&clusters, brc8::br_cluster8_kernel<L>, &cfg) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
   return clusters;
 }
+}  // namespace
+
+size_t br_cluster8_smem() { return brc8::Cfg<3>::kSmem; }
+cudaError_t launch_br_cluster8(const BrArgs &args, int clusters, cudaStream_t st) { return launch8<3>(args, clusters, st); }
+int br_cluster8_occupancy() { return occupancy8<3>(); }
+size_t br_cluster8_l2_smem() { return brc8::Cfg<2>::kSmem; }
+cudaError_t launch_br_cluster8_l2(const BrArgs &args, int clusters, cudaStream_t st) {
+  return launch8<2>(args, clusters, st);
+}
+int br_cluster8_l2_occupancy() { return occupancy8<2>(); }
 
 }  // namespace arx

@@ -278,6 +278,48 @@ __device__ __forceinline__ void make_digits4(uint32_t *D, const uint32_t *A, uin
   }
 }
 
+// The same for the gadget variant l = 2, Bg = 2^10 (10-bit digits): rounding
+// half of the 20-bit gadget plus the +512 offset of each digit; D[r][0][k] holds
+// the digits u = d + 512 of positions k and k+256 (16-bit halves), D[r][1][k]
+// those of k+512 and k+768.
+constexpr uint32_t kDecOffset2 = (1u << 11) + (512u << 22) + (512u << 12);
+__device__ __forceinline__ void make_digits_l2(uint32_t *D, const uint32_t *A, uint32_t a, int tid, int nthreads) {
+  for (int k = tid; k < 256; k += nthreads) {
+    uint32_t u0[4], u1[4];  // rows 0, 1 at position k + 256 m
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const uint32_t pos = (uint32_t)k + 256u * m;
+      const uint32_t j = (pos - a) & 2047u;
+      uint32_t v = A[j & 1023u];
+      v = (j & 1024u) ? 0u - v : v;
+      const uint32_t y = v - A[pos] + kDecOffset2;
+      u0[m] = y >> 22;
+      u1[m] = (y >> 12) & 0x3FFu;
+    }
+    D[k] = u0[0] | (u0[1] << 16);
+    D[256 + k] = u0[2] | (u0[3] << 16);
+    D[512 + k] = u1[0] | (u1[1] << 16);
+    D[768 + k] = u1[2] | (u1[3] << 16);
+  }
+}
+
+// load_first2 for 10-bit digits (rows packed by make_digits_l2; Dr = one row).
+// Out < 5q + 1024.
+__device__ __forceinline__ void load_first2_l2(uint32_t (&x)[8], const uint32_t *Dr, uint2 z1, uint2 z23, int Qf,
+                                               const PrimeRT &pr, int lane) {
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    const uint32_t d01 = Dr[lane + 32 * e], d23 = Dr[256 + lane + 32 * e];
+    const uint32_t t0 = shoup_mul(z1.x, z1.y, d23 & 0xFFFFu, pr.q);
+    const uint32_t t1 = shoup_mul(z1.x, z1.y, d23 >> 16, pr.q);
+    const uint32_t u0 = d01 & 0xFFFFu, u1 = d01 >> 16;
+    const uint32_t a = Qf < 2 ? u0 + t0 + pr.dc : u0 - t0 + pr.q2 + pr.dd;
+    const uint32_t b = Qf < 2 ? u1 + t1 + pr.dc : u1 - t1 + pr.q2 + pr.dd;
+    const uint32_t t2 = shoup_mul(z23.x, z23.y, b, pr.q);
+    x[e] = (Qf & 1) ? a - t2 + pr.q2 : a + t2;
+  }
+}
+
 // Last two inverse stages and CRT of both primes, then ACC += the Torus32
 // result: post0[Q] holds quarter Q of prime 0 (twisted, natural order), prime 1
 // lies poff1 words above it.

@@ -39,22 +39,24 @@ void parallel_for(int count, F f) {
 
 }  // namespace
 
-extern "C" int arx_client_keygen(int n, const uint8_t *s, const uint8_t *K, const uint32_t *bsk_mask,
-                                 const int32_t *bsk_noise, const uint32_t *ksk_mask, const int32_t *ksk_noise,
-                                 uint32_t *bsk, uint32_t *ksk) {
+extern "C" int arx_client_keygen_gadget(int n, int l, int bg_bits, const uint8_t *s, const uint8_t *K,
+                                        const uint32_t *bsk_mask, const int32_t *bsk_noise, const uint32_t *ksk_mask,
+                                        const int32_t *ksk_noise, uint32_t *bsk, uint32_t *ksk) {
   if (n < 1 || n > ARX_LWE_N || !s || !K || !bsk_mask || !bsk_noise || !ksk_mask || !ksk_noise || !bsk || !ksk)
     return ARX_EINVAL;
-  // BSK_i = TGSW_K(s_i): row (c, p) is (a, a K + e) plus s_i 2^(32-7p) on component c.
+  if (!((l == 3 && bg_bits == 7) || (l == 2 && bg_bits == 10))) return ARX_EINVAL;
+  const int rows = 2 * l;
+  // BSK_i = TGSW_K(s_i): row (c, p) is (a, a K + e) plus s_i 2^(32 - p bg_bits) on component c.
   parallel_for(n, [&](int i) {
-    for (int r = 0; r < ARX_BSK_ROWS; ++r) {
-      const int c = r / 3, p = r % 3 + 1;
-      const size_t src = ((size_t)i * ARX_BSK_ROWS + r) * kN;
-      uint32_t *mask = bsk + (((size_t)i * ARX_BSK_ROWS + r) * 2 + 0) * kN;
-      uint32_t *body = bsk + (((size_t)i * ARX_BSK_ROWS + r) * 2 + 1) * kN;
+    for (int r = 0; r < rows; ++r) {
+      const int c = r / l, p = r % l + 1;
+      const size_t src = ((size_t)i * rows + r) * kN;
+      uint32_t *mask = bsk + (((size_t)i * rows + r) * 2 + 0) * kN;
+      uint32_t *body = bsk + (((size_t)i * rows + r) * 2 + 1) * kN;
       std::memcpy(mask, bsk_mask + src, sizeof(uint32_t) * kN);
       for (int k = 0; k < kN; ++k) body[k] = (uint32_t)bsk_noise[src + k];
       add_times_binary(mask, K, body);
-      const uint32_t h = s[i] ? (1u << (32 - 7 * p)) : 0u;
+      const uint32_t h = s[i] ? (1u << (32 - bg_bits * p)) : 0u;
       (c == 0 ? mask : body)[0] += h;
     }
   });
@@ -78,6 +80,12 @@ extern "C" int arx_client_keygen(int n, const uint8_t *s, const uint8_t *K, cons
     }
   });
   return ARX_OK;
+}
+
+extern "C" int arx_client_keygen(int n, const uint8_t *s, const uint8_t *K, const uint32_t *bsk_mask,
+                                 const int32_t *bsk_noise, const uint32_t *ksk_mask, const int32_t *ksk_noise,
+                                 uint32_t *bsk, uint32_t *ksk) {
+  return arx_client_keygen_gadget(n, 3, 7, s, K, bsk_mask, bsk_noise, ksk_mask, ksk_noise, bsk, ksk);
 }
 
 extern "C" int arx_client_encrypt(int n, const uint8_t *s, const uint32_t *mask, const int32_t *noise,

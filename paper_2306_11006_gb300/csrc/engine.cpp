@@ -378,6 +378,7 @@ int plan_build(Engine &E, const arx_netlist *nl, int keyset, int mode, std::uniq
   std::unique_ptr<Plan> P(new Plan);
   P->keyset = keyset < 0 ? E.last : keyset;
   P->n = ks->n;
+  P->l = ks->l;
   P->mode = mode;
   P->num_inputs = nl->num_inputs;
   P->num_gates = nl->num_gates;
@@ -408,13 +409,14 @@ int plan_build(Engine &E, const arx_netlist *nl, int keyset, int mode, std::uniq
     P->levels.push_back(L);
   }
   P->bootstraps = br.size();
-  if (mode == ARX_MODE_GRAPH) {
+  if (mode == ARX_MODE_GRAPH && P->l == 3) {  // the gadget l = 2 has a single kernel
     rc = calibrate(E, P->n);
     if (rc) return rc;
   }
   size_t ks_part_max = 0, ks_gate_max = 0;
   for (Level &L : P->levels) {
-    L.shape = mode == ARX_MODE_GRAPH ? E.policy.pick(L.br_cnt, P->n) : E.policy.heuristic(L.br_cnt);
+    L.shape = ShapePolicy::for_gadget(
+        P->l, mode == ARX_MODE_GRAPH ? E.policy.pick(L.br_cnt, P->n) : E.policy.heuristic(L.br_cnt));
     L.grid = E.policy.grid(L.shape, std::max(1, L.br_cnt));
     L.ks_splits = ks_splits(L.ks_cnt, E.sms);
     if (L.ks_splits > 1) {
@@ -580,7 +582,7 @@ int bootstrap_gates(Engine &E, const uint8_t *types, const uint32_t *a, const ui
     args.tg = E.tg;
     args.status = E.status;
     args.tc = E.tc;
-    const BrShape s = E.policy.pick(args.num_jobs, ks->n);
+    const BrShape s = ShapePolicy::for_gadget(ks->l, E.policy.pick(args.num_jobs, ks->n));
     CK(launch_br(args, s, E.policy.grid(s, args.num_jobs), st));
   }
   const bool dev_out = is_device_ptr(out);
@@ -607,21 +609,24 @@ int bootstrap_gates(Engine &E, const uint8_t *types, const uint32_t *a, const ui
 // --------------------------------------------------------------------------
 // keys
 // --------------------------------------------------------------------------
-size_t keyset_bytes(int n) {
-  return (size_t)n * 6 * kChunkBytes + (size_t)kN * 8 * 3 * kKsRowStride * 4;
+size_t keyset_bytes(int n, int l) {
+  return (size_t)n * 2 * l * kChunkBytes + (size_t)kN * 8 * 3 * kKsRowStride * 4;
 }
 
-int load_keys(Engine &E, const uint32_t *bsk, const uint32_t *ksk, int n, cudaStream_t user_st) {
+int load_keys(Engine &E, const uint32_t *bsk, const uint32_t *ksk, int n, int l, cudaStream_t user_st) {
   if (!bsk || !ksk) return fail(ARX_EINVAL, "null key pointer");
   if (n < 1 || n > kMaxLweN) return fail(ARX_EINVAL, "lwe_n %d outside 1..%d", n, kMaxLweN);
-  if (E.budget && E.resident_bytes() + keyset_bytes(n) > E.budget)
+  if (l != 3 && l != 2) return fail(ARX_EINVAL, "gadget length %d: only 3 (Bg = 2^7) or 2 (Bg = 2^10)", l);
+  if (E.budget && E.resident_bytes() + keyset_bytes(n, l) > E.budget)
     return fail(ARX_ENOMEM, "key set would exceed the HBM budget");
   cudaStream_t st = user_st ? user_st : E.stream;
   Keyset K;
   K.n = n;
-  const size_t bsk_ntt = (size_t)n * 6 * kChunkBytes;
+  K.l = l;
+  const int rows = 2 * l;
+  const size_t bsk_ntt = (size_t)n * rows * kChunkBytes;
   const size_t ksk_dev = (size_t)kN * 8 * 3 * kKsRowStride * 4;
-  const size_t bsk_coef = (size_t)n * 6 * 2 * kN * 4;
+  const size_t bsk_coef = (size_t)n * rows * 2 * kN * 4;
   cudaError_t e = cudaMalloc(&K.bsk, bsk_ntt);
   if (e == cudaSuccess) e = cudaMalloc(&K.ksk, ksk_dev);
   uint32_t *tmp = nullptr;
@@ -631,7 +636,7 @@ int load_keys(Engine &E, const uint32_t *bsk, const uint32_t *ksk, int n, cudaSt
     if (e == cudaSuccess) e = cudaMemcpyAsync(tmp, bsk, bsk_coef, cudaMemcpyHostToDevice, st);
     src = tmp;
   }
-  if (e == cudaSuccess) e = launch_bsk_to_ntt(src, n, K.bsk, E.tc, E.tg, st);
+  if (e == cudaSuccess) e = launch_bsk_to_ntt(src, n, rows, K.bsk, E.tc, E.tg, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(K.ksk, 0, ksk_dev, st);
   const size_t row = (size_t)n + 1;
   for (int v = 1; v < 4 && e == cudaSuccess; ++v)
@@ -683,7 +688,7 @@ int unload_keys(Engine &E, int id) {
 size_t Engine::resident_bytes() const {
   size_t s = 0;
   for (const Keyset &k : keysets)
-    if (k.used) s += keyset_bytes(k.n);
+    if (k.used) s += keyset_bytes(k.n, k.l);
   return s;
 }
 
@@ -704,12 +709,20 @@ using namespace arx;
 
 extern "C" int arx_load_keys(const uint32_t *bsk, const uint32_t *ksk) {
   API_BEGIN
-  return load_keys(E, bsk, ksk, ARX_LWE_N, nullptr);
+  return load_keys(E, bsk, ksk, ARX_LWE_N, 3, nullptr);
 }
 
 extern "C" int arx_load_keys_ex(const uint32_t *bsk, const uint32_t *ksk, int lwe_n, void *stream) {
   API_BEGIN
-  return load_keys(E, bsk, ksk, lwe_n, (cudaStream_t)stream);
+  return load_keys(E, bsk, ksk, lwe_n, 3, (cudaStream_t)stream);
+}
+
+extern "C" int arx_load_keys_gadget(const uint32_t *bsk, const uint32_t *ksk, int lwe_n, int l, int bg_bits,
+                                    void *stream) {
+  API_BEGIN
+  if (!((l == 3 && bg_bits == 7) || (l == 2 && bg_bits == 10)))
+    return fail(ARX_EINVAL, "gadget (l %d, Bg 2^%d): only (3, 2^7) and (2, 2^10)", l, bg_bits);
+  return load_keys(E, bsk, ksk, lwe_n, l, (cudaStream_t)stream);
 }
 
 extern "C" int arx_unload_keys(int keyset) {
@@ -927,7 +940,8 @@ extern "C" int arx_set_launch_shape(int H, int GT) {
     E.policy.forced = BrShape{0, 0};
     return ARX_OK;
   }
-  if (!br_shape_supported(BrShape{H, GT})) return fail(ARX_EINVAL, "unsupported launch shape (%d, %d)", H, GT);
+  if (H == kCluster8L2H || !br_shape_supported(BrShape{H, GT}))
+    return fail(ARX_EINVAL, "unsupported launch shape (%d, %d)", H, GT);
   E.policy.forced = BrShape{H, GT};
   return ARX_OK;
 }

@@ -28,6 +28,7 @@ struct DevBuf {
 struct Keyset {
   bool used = false;
   int n = 0;
+  int l = 3;                // gadget length: 3 (Bg = 2^7) or 2 (Bg = 2^10)
   uint32_t *bsk = nullptr;  // NTT-domain bootstrapping key
   uint32_t *ksk = nullptr;  // [N][8][3][632]
   int refs = 0;             // plans referencing it
@@ -45,7 +46,7 @@ struct Level {
 };
 
 struct Plan {
-  int keyset = -1, n = 0, mode = 0;
+  int keyset = -1, n = 0, mode = 0, l = 3;
   uint32_t num_inputs = 0, num_gates = 0;
   std::vector<uint32_t> outputs;
   std::vector<Level> levels;
@@ -73,6 +74,8 @@ struct ShapePolicy {
   int occupancy(BrShape s);
   BrShape heuristic(int jobs) const;
   BrShape pick(int jobs, int n) const;
+  // key sets with gadget l = 2 have one kernel of their own
+  static BrShape for_gadget(int l, BrShape s) { return l == 2 ? BrShape{kCluster8L2H, 1} : s; }
   int grid(BrShape s, int jobs);
 };
 
@@ -106,7 +109,7 @@ void emit_gate(uint32_t type, uint32_t w0, uint32_t w1, uint32_t w2, uint32_t ou
                std::vector<KsJob> &ks, uint32_t br_base);
 int calibrate(Engine &E, int n);
 int levelize(const arx_netlist *nl, uint32_t *wave, uint32_t *depth);
-size_t keyset_bytes(int n);
+size_t keyset_bytes(int n, int l = 3);
 int reserve_ks_scratch(DevBuf &part, DevBuf &cnt, size_t jobs, int splits);
 
 }  // namespace arx

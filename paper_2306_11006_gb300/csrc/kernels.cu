@@ -51,16 +51,16 @@ __device__ void bsk_poly_to_ntt(const uint32_t *src, uint32_t *dst, uint32_t *xb
   }
 }
 
-__global__ void bsk_to_ntt_kernel(const uint32_t *__restrict__ bsk, int n, uint32_t *__restrict__ out,
+__global__ void bsk_to_ntt_kernel(const uint32_t *__restrict__ bsk, int n, int rows, uint32_t *__restrict__ out,
                                   const __grid_constant__ TwiddleConst tc, const TwiddleGlobal *tg) {
   __shared__ __align__(16) uint32_t xbuf[4][kXpose];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long wid = (long long)blockIdx.x * 4 + warp;
-  const long long total = (long long)n * 12 * 2;
+  const long long total = (long long)n * rows * 2 * 2;
   if (wid >= total) return;
-  const long long poly = wid >> 1;  // (i, r, c) in [0, n*12)
+  const long long poly = wid >> 1;  // (i, r, c) in [0, n rows 2)
   const int P = (int)(wid & 1);
-  const long long ir = poly >> 1;   // i*6 + r
+  const long long ir = poly >> 1;   // i rows + r
   const int c = (int)(poly & 1);
   const uint32_t *src = bsk + poly * kN;
   uint32_t *dst = out + ir * kChunkWords + (size_t)(c * 2 + P) * kN;
@@ -181,11 +181,11 @@ __global__ void gather_kernel(const uint32_t *__restrict__ wires, const uint32_t
 
 }  // namespace
 
-cudaError_t launch_bsk_to_ntt(const uint32_t *bsk_coef, int n, uint32_t *bsk_ntt, const TwiddleConst &tc,
+cudaError_t launch_bsk_to_ntt(const uint32_t *bsk_coef, int n, int rows, uint32_t *bsk_ntt, const TwiddleConst &tc,
                               const TwiddleGlobal *tg, cudaStream_t st) {
-  const long long warps = (long long)n * 24;
+  const long long warps = (long long)n * rows * 4;
   const int blocks = (int)((warps + 3) / 4);
-  bsk_to_ntt_kernel<<<blocks, 128, 0, st>>>(bsk_coef, n, bsk_ntt, tc, tg);
+  bsk_to_ntt_kernel<<<blocks, 128, 0, st>>>(bsk_coef, n, rows, bsk_ntt, tc, tg);
   return cudaGetLastError();
 }
 
@@ -215,6 +215,7 @@ size_t br_smem(BrShape s) {
   if (s.H == kClusterH) return s.GT == 1 ? br_cluster_smem() : 0;
   if (s.H == kCluster4H) return s.GT == 1 ? br_cluster4_smem() : 0;
   if (s.H == kCluster8H) return s.GT == 1 ? br_cluster8_smem() : 0;
+  if (s.H == kCluster8L2H) return s.GT == 1 ? br_cluster8_l2_smem() : 0;
   switch (s.H) {
     case 1: return br_smem_h1(s.GT);
     case 2: return br_smem_h2(s.GT);
@@ -230,6 +231,7 @@ int br_occupancy(BrShape s) {
   if (s.H == kClusterH) return s.GT == 1 ? br_cluster_occupancy() : 0;
   if (s.H == kCluster4H) return s.GT == 1 ? br_cluster4_occupancy() : 0;
   if (s.H == kCluster8H) return s.GT == 1 ? br_cluster8_occupancy() : 0;
+  if (s.H == kCluster8L2H) return s.GT == 1 ? br_cluster8_l2_occupancy() : 0;
   switch (s.H) {
     case 1: return br_occupancy_h1(s.GT);
     case 2: return br_occupancy_h2(s.GT);
@@ -240,7 +242,7 @@ int br_occupancy(BrShape s) {
 }
 
 int br_threads(BrShape s) {
-  if (s.H == kCluster8H) return 9 * 32;
+  if (s.H == kCluster8H || s.H == kCluster8L2H) return 9 * 32;
   return is_cluster_shape(s) ? 13 * 32 : (2 * s.H * s.GT + 1) * 32;
 }
 
@@ -249,6 +251,7 @@ cudaError_t launch_br(const BrArgs &args, BrShape s, int grid, cudaStream_t st) 
   if (s.H == kClusterH) return s.GT == 1 ? launch_br_cluster(args, grid, st) : cudaErrorInvalidValue;
   if (s.H == kCluster4H) return s.GT == 1 ? launch_br_cluster4(args, grid, st) : cudaErrorInvalidValue;
   if (s.H == kCluster8H) return s.GT == 1 ? launch_br_cluster8(args, grid, st) : cudaErrorInvalidValue;
+  if (s.H == kCluster8L2H) return s.GT == 1 ? launch_br_cluster8_l2(args, grid, st) : cudaErrorInvalidValue;
   switch (s.H) {
     case 1: return launch_br_h1(args, s.GT, grid, st);
     case 2: return launch_br_h2(args, s.GT, grid, st);

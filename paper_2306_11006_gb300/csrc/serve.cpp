@@ -42,6 +42,7 @@ struct Request {
   int id = 0;
   int keyset = -1;
   int n = 0;
+  int l = 3;  // gadget length of the key set
   const uint32_t *bsk = nullptr, *ksk = nullptr;  // captured at admission (key set pinned)
   uint32_t num_inputs = 0, num_gates = 0;
   std::vector<uint32_t> outputs;
@@ -142,6 +143,7 @@ int build_request(Engine &E, const arx_netlist *nl, int keyset, std::shared_ptr<
   auto R = std::make_shared<Request>();
   R->keyset = keyset < 0 ? E.last : keyset;
   R->n = ks->n;
+  R->l = ks->l;
   R->num_inputs = nl->num_inputs;
   R->num_gates = nl->num_gates;
   R->outputs.assign(nl->outputs, nl->outputs + nl->num_outputs);
@@ -248,7 +250,7 @@ int run_tick(Server &S, std::vector<std::shared_ptr<Request>> &act) {
       a.tg = S.tg;
       a.status = S.status;
       a.tc = S.tc;
-      const BrShape s = S.policy.pick(a.num_jobs, head.n);
+      const BrShape s = ShapePolicy::for_gadget(head.l, S.policy.pick(a.num_jobs, head.n));
       SCK(launch_br(a, s, S.policy.grid(s, a.num_jobs), S.stream));
       S.launches++;
     }

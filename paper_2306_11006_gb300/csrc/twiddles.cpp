@@ -74,6 +74,8 @@ void fill(int P, uint64_t q, TwiddleConst *tc, TwiddleGlobal *tg) {
   for (int zi = 0; zi < 32; ++zi) tc->fwd1[P][zi] = entry(zeta[zi], q);
   tc->dig_c[P] = (uint32_t)((2 * q - 64 - 64 * zeta[1] % q) % q);
   tc->dig_d[P] = (uint32_t)((64 * zeta[1] % q + q - 64) % q);
+  tc->dig_c2[P] = (uint32_t)((2 * q - 512 - 512 * zeta[1] % q) % q);
+  tc->dig_d2[P] = (uint32_t)((512 * zeta[1] % q + q - 512) % q);
   // forward pass 2, per lane: stage s (length 16 >> s) has 2^s blocks per lane;
   // block b of lane l is zeta index 2^s (32 + l) + b, stored at [(2^s - 1 + b)][l].
   for (int s = 0; s < 5; ++s)

@@ -110,6 +110,25 @@ def test_client_keygen_matches_oracle(O, n, seed):
     assert np.array_equal(ksk, oksk)
 
 
+@pytest.mark.parametrize("n", [5, 512])
+def test_client_keygen_gadget_l2_matches_oracle(O, n):
+    kr = I.key_randomness(8, n, l=2)
+    bsk, ksk = arx.client_keygen(kr)
+    assert bsk.shape == (n, 4, 2, 1024)
+    obsk, oksk = O.keygen(kr)
+    assert np.array_equal(bsk, obsk)
+    assert np.array_equal(ksk, oksk)
+
+
+def test_client_keygen_rejects_other_gadgets():
+    kr = I.key_randomness(8, 4)
+    arrs = [np.ascontiguousarray(a) for a in (kr.s, kr.K, kr.bsk_mask, kr.bsk_noise, kr.ksk_mask, kr.ksk_noise)]
+    out = np.zeros((4, 6, 2, 1024), np.uint32), np.zeros((1024, 8, 4, 5), np.uint32)
+    rc = arx.lib().arx_client_keygen_gadget(4, 3, 10, *[arx._ptr(a) for a in arrs], arx._ptr(out[0]),
+                                            arx._ptr(out[1]))
+    assert rc == -1  # ARX_EINVAL
+
+
 def test_client_encrypt_decrypt_match_oracle(O):
     n = 630
     kr = I.key_randomness(3, n)

@@ -36,6 +36,11 @@ def _loaded64(torch_cuda, keys64):
     return arx.load_keys(keys64.bsk, keys64.ksk, 64)
 
 
+@pytest.fixture(scope="session")
+def _loaded512_l2(torch_cuda, keys512_l2):
+    return arx.load_keys(keys512_l2.bsk, keys512_l2.ksk, 512, l=2)
+
+
 @pytest.fixture
 def gpu630(_loaded630):
     arx.use_keys(_loaded630)   # the default key set of the calls without an id
@@ -364,3 +369,52 @@ def test_plan_keeps_keyset_busy(gpu630, keys64, torch_cuda):
     p.close()
     arx.unload_keys(ks)
     arx.use_keys(gpu630)
+
+
+# --------------------------------------------------------------------------
+# the paper's own parameter set: n = 512, gadget l = 2 (Bg = 2^10)
+# --------------------------------------------------------------------------
+def test_gadget_l2_all_gate_types_bit_exact(O, keys512_l2, _loaded512_l2):
+    k, ks = keys512_l2, _loaded512_l2
+    types = np.array([t for t in range(11) for _ in range(4)], np.uint8)
+    xs, ys, zs = (I.random_bits(400 + j, len(types)) for j in range(3))
+    ca, cb, cc = (k.encrypt(O, I, v, 410 + j) for j, v in enumerate((xs, ys, zs)))
+    out = np.zeros_like(ca)
+    arx.bootstrap_gates_ex(types, ca, cb, cc, out, keyset=ks)
+    assert np.array_equal(out, k.ctx.gates(types, ca, cb, cc))
+    assert np.array_equal(arx.client_decrypt(512, k.s, out), _truth(types, xs, ys, zs))
+
+
+@pytest.mark.parametrize("mode", [arx.MODE_PLAIN, arx.MODE_GRAPH])
+def test_gadget_l2_netlist_and_shapes(O, keys512_l2, _loaded512_l2, mode):
+    k, ks = keys512_l2, _loaded512_l2
+    nl = I.union([I.ripple_carry_adder(4), I.comparator(3)])
+    bits = I.random_bits(420, nl.num_inputs)
+    ct = k.encrypt(O, I, bits, 421)
+    out = np.zeros((len(nl.outputs), 513), np.uint32)
+    with arx.Plan(nl, keyset=ks, mode=mode) as p:
+        assert all((H, GT) == (40, 1) for H, GT, j in p.shapes() if j)
+        p.run(ct, out)
+    assert np.array_equal(out, k.ctx.eval_netlist(nl, ct))
+    assert np.array_equal(arx.client_decrypt(512, k.s, out), nl.plain_eval(bits))
+
+
+def test_gadget_l2_wave_wider_than_the_device_sampled(O, keys512_l2, _loaded512_l2):
+    # more gates than co-resident eight-CTA clusters: the persistent loop takes
+    # several tiles per cluster
+    k, ks = keys512_l2, _loaded512_l2
+    types = I.random_gate_types(430, 40)
+    xs, ys = I.random_bits(431, 40), I.random_bits(432, 40)
+    ca, cb = k.encrypt(O, I, xs, 433), k.encrypt(O, I, ys, 434)
+    out = np.zeros_like(ca)
+    arx.bootstrap_gates_ex(types, ca, cb, ca, out, keyset=ks)
+    assert np.array_equal(arx.client_decrypt(512, k.s, out), _truth(types, xs, ys, xs))
+    pick = np.array([0, 13, 26, 39])
+    assert np.array_equal(out[pick], k.ctx.gates(types[pick], ca[pick], cb[pick]))
+
+
+def test_gadget_l2_shape_is_not_an_override(gpu630):
+    with pytest.raises(arx.ArxError):
+        arx.set_launch_shape(40, 1)
+    with pytest.raises(arx.ArxError):
+        arx._check(arx.lib().arx_load_keys_gadget(None, None, 512, 2, 7, None))
