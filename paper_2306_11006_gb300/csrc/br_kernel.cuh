@@ -4,13 +4,16 @@
 //   CMux external products, sample extraction (Fig. 2 and Sec. 2.2 of the paper).
 //   Each br_h*.cu translation unit instantiates the shapes of one H.
 //
-// Blind rotation kernel organisation.  A gate is processed by 2H consumer warps:
-// warp (P, h) carries prime P of the CRT pair and the h-th group of 6/H TGSW rows.
+// Blind rotation kernel organisation.  A gate is processed by 2H warps: warp
+// (P, h) carries prime P of the CRT pair and the h-th group of 6/H TGSW rows.
 // GT gates share a CTA so that every bootstrapping-key row (16 KiB: two output
-// polynomials x two primes) is brought into shared memory once per CTA by a
-// producer warp (cp.async.bulk into a 4-stage mbarrier ring) and read by all
-// 2 GT warps that use it.  Every wait is bounded: on a timeout the kernel records
-// kDevTimeout in the device status word, stops waiting, runs to the end and returns.
+// polynomials x two primes) is brought into shared memory once per CTA
+// (cp.async.bulk into a 4..8-stage mbarrier ring) and read by all 2 GT warps that
+// use it.  There is no producer warp: the last of those warps to finish with a
+// slot refills it with the row kStages ahead, so a CTA of 12 warps keeps three
+// warps per scheduler and 168 registers a thread.  Every wait is bounded: on a
+// timeout the kernel records kDevTimeout in the device status word, stops
+// waiting, runs to the end, lets its copies in flight land and returns.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -135,7 +138,9 @@ struct BrShared {
   uint32_t *dig;      // GT x [2][N] packed gadget digits
   uint32_t *scratch;  // consumer warps x kScratch
   uint16_t *abar;     // GT x kAbarPitch
-  uint64_t *full, *empty;
+  uint64_t *full;     // kStages: row landed (transaction count)
+  uint32_t *cnt;      // kStages: warps done with the slot's current row
+  uint32_t *issued;   // kStages: 1 + the last row copied into the slot
   volatile int *abort_flag;
 };
 
@@ -172,12 +177,33 @@ __device__ __forceinline__ BrShared br_carve(uint8_t *smem) {
   s.scratch = s.dig + GT * 2 * kN;
   s.abar = reinterpret_cast<uint16_t *>(s.scratch + 2 * H * GT * scratch_words<H>());
   s.full = reinterpret_cast<uint64_t *>(s.abar + GT * kAbarPitch);
-  s.empty = s.full + kStages;
-  s.abort_flag = reinterpret_cast<volatile int *>(s.empty + kStages);
+  s.cnt = reinterpret_cast<uint32_t *>(s.full + kStages);
+  s.issued = s.cnt + kStages;
+  s.abort_flag = reinterpret_cast<volatile int *>(s.issued + kStages);
   return s;
 }
 
-// One consumer warp (prime P, row group h) over all tiles of the launch.  The
+// Key rows this CTA consumes: 6 n per tile of GT gates.
+template <int GT>
+__device__ __forceinline__ uint32_t cta_rows(const BrArgs &args) {
+  const int tiles = (args.num_jobs + GT - 1) / GT;
+  const int mine = (int)blockIdx.x < tiles ? (tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  return (uint32_t)mine * 6u * (uint32_t)args.n;
+}
+
+// Copy key row jc of the CTA's sequence (row jc mod 6n of the key: CMux i,
+// TGSW row r) into its ring slot.
+template <int kStages>
+__device__ __forceinline__ void issue_row(const BrShared &S, const BrArgs &args, uint32_t jc) {
+  const uint32_t slot = jc % kStages;
+  S.issued[slot] = jc + 1u;
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic reads of the slot before the copy
+  mbar_expect_tx(S.full + slot, kChunkBytes);
+  bulk_g2s(S.ring + slot * kChunkWords, args.bsk + (size_t)(jc % (6u * (uint32_t)args.n)) * kChunkWords,
+           kChunkBytes, S.full + slot);
+}
+
+// One warp (prime P, row group h) over all tiles of the launch.  The
 // same code serves both primes; the owner of output c (warp (P, c) for H > 1,
 // both outputs for H = 1) keeps that output's accumulator in acc0.
 template <int H, int GT>
@@ -203,6 +229,7 @@ __device__ __forceinline__ void br_consumer(const BrShared &S, const BrArgs &arg
   const uint2 *tw2i = args.tg->inv2[P];
   const uint2 *twist = args.tg->twist[P];
   const int tiles = (args.num_jobs + GT - 1) / GT;
+  const uint32_t rows = cta_rows<GT>(args);
   uint32_t it = 0;
 
   for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++it) {
@@ -260,7 +287,14 @@ __device__ __forceinline__ void br_consumer(const BrShared &S, const BrArgs &arg
           acc1[4 * e4 + 3] += mont_mul(x[4 * e4 + 3], b1.w, pr);
         }
         __syncwarp();
-        if (lane == 0) mbar_arrive(S.empty + slot);
+        if (lane == 0) {  // the slot's last user refills it
+          __threadfence_block();
+          if (atomicAdd(S.cnt + slot, 1u) == 2u * GT - 1u) {
+            __threadfence_block();
+            S.cnt[slot] = 0u;
+            if (jc + kStages < rows) issue_row<kStages>(S, args, jc + kStages);
+          }
+        }
       }
 
       // prime P combines coefficients e in [16 P, 16 P + 16) and sends the other half;
@@ -344,17 +378,17 @@ __device__ __forceinline__ void br_consumer(const BrShared &S, const BrArgs &arg
 }
 
 template <int H, int GT>
-__global__ void __launch_bounds__((2 * H * GT + 1) * 32, 1) br_kernel(const __grid_constant__ BrArgs args) {
+__global__ void __launch_bounds__(2 * H * GT * 32, 1) br_kernel(const __grid_constant__ BrArgs args) {
   extern __shared__ __align__(128) uint8_t smem[];
   BrShared S = br_carve<H, GT>(smem);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  constexpr int kCons = 2 * H * GT;
   constexpr int kStages = br_stages<H, GT>();
   static_assert(kStages >= 4 && kStages <= 8, "ring depth");
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(S.full + s, 1);
-      mbar_init(S.empty + s, 2 * GT);
+      S.cnt[s] = 0u;
+      S.issued[s] = 0u;
     }
     *S.abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -362,38 +396,22 @@ __global__ void __launch_bounds__((2 * H * GT + 1) * 32, 1) br_kernel(const __gr
   __syncthreads();
   if (threadIdx.x == 0) stamp_start(args.stamps);
   if (args.num_jobs <= 0) return;
-
-  if (warp == kCons) {  // producer: stream BSK rows into the ring
-    if (lane == 0) {
-      const int tiles = (args.num_jobs + GT - 1) / GT;
-      uint32_t jc = 0;
-      bool ok = true;
-      for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
-        for (int i = 0; i < args.n && ok; ++i) {
-          for (int r = 0; r < 6; ++r, ++jc) {
-            const uint32_t slot = jc % kStages;
-            if (jc >= (uint32_t)kStages && !mbar_wait(S.empty + slot, ((jc / kStages) - 1) & 1u, S.abort_flag, args.status)) {
-              ok = false;
-              break;
-            }
-            mbar_expect_tx(S.full + slot, kChunkBytes);
-            bulk_g2s(S.ring + slot * kChunkWords, args.bsk + ((size_t)i * 6 + r) * kChunkWords, kChunkBytes,
-                     S.full + slot);
-          }
-        }
-      }
-      if (!ok) {  // drain copies still in flight (bounded) before the CTA retires
-        for (uint32_t k = jc > (uint32_t)kStages ? jc - kStages : 0; k < jc; ++k) {
-          long long t0 = clock64();
-          while (!mbar_try_wait(S.full + (k % kStages), (k / kStages) & 1u) && clock64() - t0 < kWaitCycles) {
-          }
-        }
-      }
-    }
-    return;
+  if (threadIdx.x == 0) {  // the first kStages rows; later ones are issued by the warps
+    const uint32_t rows = cta_rows<GT>(args);
+    for (uint32_t jc = 0; jc < (uint32_t)kStages && jc < rows; ++jc) issue_row<kStages>(S, args, jc);
   }
   const int g = warp / (2 * H), role = warp % (2 * H);
   br_consumer<H, GT>(S, args, g, role >> 1, role & 1, lane);
+  __syncthreads();
+  if (threadIdx.x == 0 && *S.abort_flag) {  // after a timeout: let copies in flight land (bounded)
+    for (int s = 0; s < kStages; ++s) {
+      const uint32_t k = S.issued[s];
+      if (k == 0u) continue;
+      const long long t0 = clock64();
+      while (!mbar_try_wait(S.full + s, ((k - 1u) / kStages) & 1u) && clock64() - t0 < kWaitCycles) {
+      }
+    }
+  }
   if (lane == 0) stamp_end(args.stamps);
 }
 
@@ -411,7 +429,7 @@ template <int H, int GT>
 cudaError_t launch_shape(const BrArgs &args, int grid, cudaStream_t st) {
   cudaError_t e = prepare_shape<H, GT>();
   if (e != cudaSuccess) return e;
-  br_kernel<H, GT><<<grid, (2 * H * GT + 1) * 32, br_smem_bytes<H, GT>(), st>>>(args);
+  br_kernel<H, GT><<<grid, 2 * H * GT * 32, br_smem_bytes<H, GT>(), st>>>(args);
   return cudaGetLastError();
 }
 
@@ -423,7 +441,7 @@ int occupancy_shape() {
     return 0;
   }
   int blocks = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, br_kernel<H, GT>, (2 * H * GT + 1) * 32,
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, br_kernel<H, GT>, 2 * H * GT * 32,
                                                     br_smem_bytes<H, GT>()) != cudaSuccess) {
     cudaGetLastError();
     return 0;

@@ -243,7 +243,7 @@ int br_occupancy(BrShape s) {
 
 int br_threads(BrShape s) {
   if (s.H == kCluster8H || s.H == kCluster8L2H) return 9 * 32;
-  return is_cluster_shape(s) ? 13 * 32 : (2 * s.H * s.GT + 1) * 32;
+  return is_cluster_shape(s) ? 13 * 32 : 2 * s.H * s.GT * 32;
 }
 
 cudaError_t launch_br(const BrArgs &args, BrShape s, int grid, cudaStream_t st) {
