@@ -137,9 +137,17 @@ constexpr int kCluster8L2H = 40;
 size_t br_cluster8_l2_smem();
 cudaError_t launch_br_cluster8_l2(const BrArgs &args, int clusters, cudaStream_t st);
 int br_cluster8_l2_occupancy();
+// Cluster shape {kCluster16H, 1}: one gate on a cluster of sixteen CTAs (a
+// non-portable cluster size; occupancy 0 where the device refuses it).
+constexpr int kCluster16H = 96;
+size_t br_cluster16_smem();
+cudaError_t launch_br_cluster16(const BrArgs &args, int clusters, cudaStream_t st);
+int br_cluster16_occupancy();
 inline bool is_cluster_shape(BrShape s) {
-  return s.H == kClusterH || s.H == kCluster4H || s.H == kCluster8H || s.H == kCluster8L2H;
+  return s.H == kClusterH || s.H == kCluster4H || s.H == kCluster8H || s.H == kCluster8L2H || s.H == kCluster16H;
 }
+// Shapes reserved for key sets with gadget l = 2 (never an override).
+inline bool is_l2_shape(BrShape s) { return s.H == kCluster8L2H; }
 
 // per-shape launchers (one translation unit per H)
 cudaError_t launch_br_h1(const BrArgs &args, int GT, int grid, cudaStream_t st);

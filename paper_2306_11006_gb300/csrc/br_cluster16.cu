@@ -1,0 +1,353 @@
+// br_cluster16.cu -- blind rotation of one gate on a cluster of sixteen CTAs
+// (sixteen SMs, a non-portable cluster size), for the narrowest waves.
+//
+// The paper runs one gate per SM and names spreading a gate over several SMs as
+// the remedy for thin waves (Sec. 8).  Here CTA (h, Q, P) of the cluster (rank
+// 4 Q + 2 P + h) owns accumulator component ACC_h, the TGSW rows whose digits
+// come from it (rows L h .. L h + L - 1), spectral quarter Q and one CRT prime P:
+// the eight-CTA kernel's work split once more, by prime, so that each of a
+// CTA's forward warps has a scheduler of its own.
+//
+// Per CMux: L forward warps (one per row) take the first two forward stages on
+// the packed digit load and run the quarter-Q transform of their row in prime
+// P; each adds its key products for output 1-h into CTA (1-h, Q, P)'s receive
+// slot with a bulk reduction (1 KiB) and keeps those for output h.  The inverse
+// warp sums the L local rows and the slot (quarter Q of output h in prime P),
+// runs the inverse quarter transform (all stages but the last two, then the
+// quarter's share of the output twist) and posts it here and at the seven CTAs
+// (h, Q', P') (1 KiB each).  All eight CTAs of component h then fold the last
+// two stages, run the CRT and update identical copies of ACC_h.  Every
+// cross-CTA dependency is a transaction count on an mbarrier (double-buffered
+// by CMux parity); every wait is bounded.  Template on the gadget length L, as
+// the eight-CTA kernel, but built for L = 3 only: with L = 2 the eight-CTA
+// kernel's four forward warps already have a scheduler each, and the extra
+// exchange partners made this split slower there (measured).
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "br_cluster_common.cuh"
+
+namespace arx {
+namespace brc16 {
+
+using namespace clu;
+
+constexpr int kClusterSize = 16;
+constexpr int kCons = 8;                    // L forward warps, the inverse warp, helpers for digits and CRT
+constexpr int kInvWarp = 3;                 // a scheduler of its own
+constexpr int kThreads = (kCons + 1) * 32;  // + producer warp
+constexpr int kConsThreads = kCons * 32;    // 256
+constexpr int kStages = 6;                  // ring of 8 KiB key rows (one prime, both outputs)
+constexpr int kRowWords = 2 * kN;
+constexpr uint32_t kRowBytes = kRowWords * 4;
+constexpr int kAbarPitch = 640;
+constexpr int kQuarter = 256;
+constexpr uint32_t kPartnerBytes = 7 * kQuarter * 4;  // seven partners, one quarter each
+
+template <int L>
+struct Cfg {
+  static constexpr uint32_t kPeerBytes = L * kQuarter * 4;         // the peer's L row products
+  static constexpr size_t kRingBytes = (size_t)kStages * kRowBytes;
+  static constexpr size_t kAccBytes = kN * 4;
+  static constexpr size_t kDigBytes = (L == 3 ? 3 * 256 : 4 * 256) * 4;
+  static constexpr size_t kOwnBytes = (size_t)L * kQuarter * 4;       // [row][quarter Q] products for output h
+  static constexpr size_t kOthBytes = (size_t)2 * L * kQuarter * 4;   // [parity][row] for output 1-h
+  static constexpr size_t kSlotBytes = (size_t)2 * kQuarter * 4;      // [parity] the peer's row sum
+  static constexpr size_t kPostBytes = (size_t)2 * 2 * 4 * kQuarter * 4;  // [parity][prime][quarter][k]
+  static constexpr size_t kScrBytes = (size_t)kCons * kQuarter * 4;
+  static constexpr size_t kAbarBytes = kAbarPitch * 2;
+  static constexpr size_t kBarBytes = (2 * kStages + 4) * 8 + 16;
+  static constexpr size_t kSmem = kRingBytes + kAccBytes + kDigBytes + kOwnBytes + kOthBytes + kSlotBytes +
+                                  kPostBytes + kScrBytes + kAbarBytes + kBarBytes;
+};
+
+template <int L>
+__global__ void __launch_bounds__(kThreads, 1) br_cluster16_kernel(const __grid_constant__ BrArgs args) {
+  using C = Cfg<L>;
+  extern __shared__ __align__(128) uint8_t smem[];
+  uint32_t *ring = reinterpret_cast<uint32_t *>(smem);  // [stage][output][N]
+  uint32_t *A = reinterpret_cast<uint32_t *>(smem + C::kRingBytes);
+  uint32_t *D = A + kN;                          // packed digits
+  uint32_t *own = D + C::kDigBytes / 4;          // [row][256], swizzled (swp)
+  uint32_t *oth = own + L * kQuarter;            // [parity][row][256], same layout
+  uint32_t *slots = oth + 2 * L * kQuarter;      // [parity][256], same layout, zero between uses
+  uint32_t *post = slots + 2 * kQuarter;         // [parity][prime][quarter][256], natural order
+  uint32_t *scratch = post + 16 * kQuarter;      // [warp][256]
+  uint16_t *abar = reinterpret_cast<uint16_t *>(scratch + kCons * kQuarter);
+  uint64_t *full = reinterpret_cast<uint64_t *>(abar + kAbarPitch);
+  uint64_t *empty = full + kStages;
+  uint64_t *done1 = empty + kStages;             // [parity]: the peer's row sum in place
+  uint64_t *done2 = done1 + 2;                   // [parity]: the partners' inverse quarters in place
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(done2 + 2);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_rank();
+  const uint32_t h = rank & 1u;                  // accumulator component
+  const int P = (int)((rank >> 1) & 1u);         // CRT prime
+  const int Q = (int)(rank >> 2);                // spectral quarter
+  const uint32_t peer = rank ^ 1u;               // (1-h, Q, P)
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(full + s, 1);
+      mbar_init(empty + s, 1);  // the forward warp of the row
+    }
+    for (int p = 0; p < 2; ++p) {
+      mbar_init(done1 + p, 1);  // one local arrival (with the expected bytes) per CMux
+      mbar_init(done2 + p, 1);
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  for (int k = threadIdx.x; k < 2 * kQuarter; k += kThreads) slots[k] = 0u;
+  fence_proxy_async_smem();
+  cluster_sync_all();  // all sixteen CTAs initialised before any remote access
+  if (threadIdx.x == 0) stamp_start(args.stamps);
+
+  const int n = args.n;
+  const int nclusters = gridDim.x / kClusterSize, cid = blockIdx.x / kClusterSize;
+  const int tiles = args.num_jobs;
+
+  if (warp == kCons) {  // producer: the L key rows of component h, prime P, for every CMux
+    if (lane == 0 && tiles > 0) {
+      uint32_t jc = 0;
+      bool ok = true;
+      for (int tile = cid; tile < tiles && ok; tile += nclusters) {
+        for (int i = 0; i < n && ok; ++i) {
+          for (int rr = 0; rr < L; ++rr, ++jc) {
+            const uint32_t slot = jc % kStages;
+            if (jc >= (uint32_t)kStages &&
+                !mbar_wait(empty + slot, ((jc / kStages) - 1) & 1u, abort_flag, args.status)) {
+              ok = false;
+              break;
+            }
+            mbar_expect_tx(full + slot, kRowBytes);
+            const uint32_t *row = args.bsk + ((size_t)i * 2 * L + L * h + rr) * kChunkWords;
+#pragma unroll
+            for (int c = 0; c < 2; ++c)  // key row layout [output][prime][N]
+              bulk_g2s(ring + slot * kRowWords + c * kN, row + (c * 2 + P) * kN, kN * 4u, full + slot);
+          }
+        }
+      }
+      if (!ok) {
+        for (uint32_t k = jc > (uint32_t)kStages ? jc - kStages : 0; k < jc; ++k) {
+          const long long t0 = clock64();
+          while (!mbar_try_wait(full + (k % kStages), (k / kStages) & 1u) && clock64() - t0 < kWaitCycles) {
+          }
+        }
+      }
+    }
+  } else if (tiles > 0) {
+    const bool fwd = warp < L;
+    const int rr = fwd ? warp : 0;  // forward warps: row L h + rr
+    const int tid = threadIdx.x;    // 0 .. 255
+    PrimeRT pr = prime_rt(P, args.tc);
+    if (L == 2) {  // first-stage offsets of 10-bit digits
+      pr.dc = args.tc.dig_c2[P];
+      pr.dd = args.tc.dig_d2[P];
+    }
+    uint32_t *myscr = scratch + warp * kQuarter;
+    const uint2 *tw1f = args.tc.fwd1[P], *tw1i = args.tc.inv1[P];
+    const uint2 z1 = args.tc.fwd1[P][1], z23 = args.tc.fwd1[P][2 + (Q >> 1)];
+    const int fb = fwd_block8(lane);
+    // loop-invariant per-lane twiddles
+    uint2 zc[7], zq[7], zi[7], z2[6], zt[8];
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+      zc[k] = __ldg(args.tg->fwdc[P][Q] + k * 32 + lane);
+      zq[k] = __ldg(args.tg->fwdq[P][Q] + k * 32 + lane);
+      zi[k] = __ldg(args.tg->invc[P] + k * 32 + lane);
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) z2[k] = __ldg(args.tg->inv2[P] + (k + 1) * 32 + lane);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) zt[e] = __ldg(args.tg->fint[P][Q] + lane + 32 * e);
+    uint32_t it = 0, cm = 0;  // tile counter, CMux counter
+    for (int tile = cid; tile < tiles; tile += nclusters, ++it) {
+      const BrJob jb = args.jobs[tile];
+      const uint32_t *wa = args.wires + (size_t)jb.ia * kWireStride;
+      const uint32_t *wb = args.wires + (size_t)jb.ib * kWireStride;
+      const uint32_t sa = (uint32_t)(int32_t)jb.sa, sb = (uint32_t)(int32_t)jb.sb;
+      for (int k = tid; k < n; k += kConsThreads) abar[k] = (uint16_t)modswitch(sa * wa[k] + sb * wb[k]);
+      const uint32_t bbar = modswitch(jb.cst + sa * wa[n] + sb * wb[n]);
+      const uint32_t shift = (2u * kN - bbar) & (2u * kN - 1);
+      // ACC_0 = 0, ACC_1 = X^-bbar testv
+      for (int k = tid; k < kN; k += kConsThreads)
+        A[k] = h == 0 ? 0u : ((((uint32_t)k - shift) & (2u * kN - 1)) < (uint32_t)kN ? kMu : 0u - kMu);
+      named_bar(1, kConsThreads);
+
+      for (int i = 0; i < n; ++i, ++cm) {
+        const uint32_t par = cm & 1u, ph = (cm >> 1) & 1u;
+        if (L == 3)
+          make_digits4(D, A, abar[i], tid, kConsThreads);
+        else
+          make_digits_l2(D, A, abar[i], tid, kConsThreads);
+        named_bar(1, kConsThreads);
+        if (fwd) {
+          uint32_t x[8];
+          if (L == 3)
+            load_first2(x, D + rr * 256, z1, z23, Q, pr, lane);
+          else
+            load_first2_l2(x, D + rr * 512, z1, z23, Q, pr, lane);
+          fwd_quarter_r(x, myscr, tw1f, zc, zq, Q, pr, lane);
+          const uint32_t jc = (it * (uint32_t)n + (uint32_t)i) * (uint32_t)L + (uint32_t)rr;
+          const uint32_t slot = jc % kStages;
+          mbar_wait(full + slot, (jc / kStages) & 1u, abort_flag, args.status);
+          // key row layout: position 32 L + E at word ((E >> 2) * 32 + L) * 4 + (E & 3)
+          const uint4 *Bown = reinterpret_cast<const uint4 *>(ring + slot * kRowWords + h * kN);
+          const uint4 *Both = reinterpret_cast<const uint4 *>(ring + slot * kRowWords + (1 - h) * kN);
+          uint32_t *oq = oth + (par * L + rr) * kQuarter;
+          uint4 *oth4 = reinterpret_cast<uint4 *>(oq);
+          uint4 *own4 = reinterpret_cast<uint4 *>(own + rr * kQuarter);
+          // products for the peer's output first: added into its slot while the rest runs
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            const uint4 b1 = Both[(2 * (fb & 3) + c) * 32 + 8 * Q + (fb >> 2)];
+            oth4[swp(8 * fb + 4 * c) >> 2] =
+                make_uint4(mont_mul(x[4 * c + 0], b1.x, pr), mont_mul(x[4 * c + 1], b1.y, pr),
+                           mont_mul(x[4 * c + 2], b1.z, pr), mont_mul(x[4 * c + 3], b1.w, pr));
+          }
+          fence_proxy_async_smem();
+          __syncwarp();
+          if (lane == 0)
+            bulk_add_s2peer(map_peer(smem_u32(slots + par * kQuarter), peer), oq, kQuarter * 4u,
+                            map_peer(smem_u32(done1 + par), peer));
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            const uint4 b0 = Bown[(2 * (fb & 3) + c) * 32 + 8 * Q + (fb >> 2)];
+            own4[swp(8 * fb + 4 * c) >> 2] =
+                make_uint4(mont_mul(x[4 * c + 0], b0.x, pr), mont_mul(x[4 * c + 1], b0.y, pr),
+                           mont_mul(x[4 * c + 2], b0.z, pr), mont_mul(x[4 * c + 3], b0.w, pr));
+          }
+          __syncwarp();
+          if (lane == 0) mbar_arrive_cta(empty + slot);
+          named_bar_arrive(2, 32 * (L + 1));  // the L rows of output h, quarter Q, in place
+        } else if (warp == kInvWarp) {
+          if (lane == 0) {
+            mbar_expect_tx(done1 + par, C::kPeerBytes);
+            mbar_expect_tx(done2 + par, kPartnerBytes);
+          }
+          named_bar(2, 32 * (L + 1));
+          // quarter Q of output h in prime P: L local rows and the peer's sum
+          mbar_wait(done1 + par, ph, abort_flag, args.status);
+          uint32_t y[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) y[e] = 0u;
+#pragma unroll
+          for (int r4 = 0; r4 <= L; ++r4) {
+            uint4 *sl = reinterpret_cast<uint4 *>(r4 < L ? own + r4 * kQuarter : slots + par * kQuarter);
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+              const int ci = swp(8 * lane + 4 * c) >> 2;
+              const uint4 q = sl[ci];
+              y[4 * c + 0] += q.x;
+              y[4 * c + 1] += q.y;
+              y[4 * c + 2] += q.z;
+              y[4 * c + 3] += q.w;
+              if (r4 == L) sl[ci] = make_uint4(0u, 0u, 0u, 0u);  // the slot starts its next use at zero
+            }
+          }
+          fence_proxy_async_smem();  // the zeroes precede the peer's next bulk additions
+          inv_quarter_r(y, myscr, tw1i, zi, z2, zt, pr, lane);
+          // post the quarter here and at the seven CTAs (h, Q', P') (ranks rank ^ 2 j)
+          uint32_t *pq = post + ((par * 2 + P) * 4 + Q) * kQuarter;
+#pragma unroll
+          for (int e = 0; e < 8; ++e) pq[lane + 32 * e] = y[e];
+          fence_proxy_async_smem();
+          __syncwarp();
+          if (lane < 7) {
+            const uint32_t dst = rank ^ (2u * (uint32_t)(lane + 1));
+            bulk_s2peer(map_peer(smem_u32(pq), dst), pq, kQuarter * 4u, map_peer(smem_u32(done2 + par), dst));
+          }
+        }
+        mbar_wait(done2 + par, ph, abort_flag, args.status);
+        named_bar(1, kConsThreads);  // all four quarters of both primes posted
+        {
+          const uint32_t *pp = post + par * 2 * 4 * kQuarter;
+          const uint32_t *post0[4] = {pp, pp + kQuarter, pp + 2 * kQuarter, pp + 3 * kQuarter};
+          crt_update(A, post0, 4 * kQuarter, args, tid, kConsThreads);
+        }
+        named_bar(1, kConsThreads);  // ACC_h updated
+      }
+      // sample extraction (quarter 0, prime 0): CTA (0, 0, 0) holds the mask a' (from ACC_0), CTA (1, 0, 0) the body b'
+      uint32_t *o = args.out + (size_t)tile * kOutStride;
+      if (Q == 0 && P == 0) {
+        if (h == 0) {
+          for (int k = tid; k < kN; k += kConsThreads) o[k] = k == 0 ? A[0] : 0u - A[kN - k];
+        } else if (tid == 0) {
+          o[kN] = A[0];
+        }
+      }
+      named_bar(1, kConsThreads);
+    }
+  }
+  __syncwarp();
+  cluster_sync_all();  // no CTA leaves while another may still touch its shared memory
+  if (threadIdx.x == 0) stamp_end(args.stamps);
+}
+
+}  // namespace brc16
+
+namespace {
+template <int L>
+cudaError_t prepare16() {
+  static bool attr = false;  // calls are serialised by the engine lock
+  if (attr) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(brc16::br_cluster16_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)brc16::Cfg<L>::kSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(brc16::br_cluster16_kernel<L>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e == cudaSuccess) attr = true;
+  return e;
+}
+
+template <int L>
+cudaLaunchConfig_t config16(int clusters, cudaStream_t st, cudaLaunchAttribute *at) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(brc16::kClusterSize * clusters, 1, 1);
+  cfg.blockDim = dim3(brc16::kThreads, 1, 1);
+  cfg.dynamicSmemBytes = brc16::Cfg<L>::kSmem;
+  cfg.stream = st;
+  at->id = cudaLaunchAttributeClusterDimension;
+  at->val.clusterDim.x = brc16::kClusterSize;
+  at->val.clusterDim.y = 1;
+  at->val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cfg;
+}
+
+template <int L>
+cudaError_t launch16(const BrArgs &args, int clusters, cudaStream_t st) {
+  cudaError_t e = prepare16<L>();
+  if (e != cudaSuccess) return e;
+  cudaLaunchAttribute at;
+  cudaLaunchConfig_t cfg = config16<L>(clusters, st, &at);
+  return cudaLaunchKernelEx(&cfg, brc16::br_cluster16_kernel<L>, args);
+}
+
+// Co-resident sixteen-CTA clusters (0 where the device does not allow them).
+template <int L>
+int occupancy16() {
+  if (prepare16<L>() != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  cudaLaunchAttribute at;
+  cudaLaunchConfig_t cfg = config16<L>(1, nullptr, &at);
+  int clusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&clusters, brc16::br_cluster16_kernel<L>, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return clusters;
+}
+}  // namespace
+
+size_t br_cluster16_smem() { return brc16::Cfg<3>::kSmem; }
+cudaError_t launch_br_cluster16(const BrArgs &args, int clusters, cudaStream_t st) {
+  return launch16<3>(args, clusters, st);
+}
+int br_cluster16_occupancy() { return occupancy16<3>(); }
+
+}  // namespace arx

@@ -59,107 +59,6 @@ struct Cfg {
                                   kPostBytes + kScrBytes + kAbarBytes + kBarBytes;
 };
 
-// Forward quarter transform with its per-lane twiddles in registers (zc: middle
-// pass, lengths 32, 16, 8; zq: last pass, lengths 4, 2, 1; same entries as the
-// global tables fwdc / fwdq).  In / out as fwd_quarter of the four-CTA kernel:
-// x[e] at p = lane + 32 e (< 5q + 128) -> spectral position 256 Q + 8 b + e,
-// b = fwd_block8(lane) (< 22q).
-__device__ __forceinline__ void fwd_quarter_r(uint32_t (&x)[8], uint32_t *xbuf, const uint2 *tw1,
-                                              const uint2 (&zc)[7], const uint2 (&zq)[7], int Q, const PrimeRT &pr,
-                                              int lane) {
-#pragma unroll
-  for (int s = 0; s < 2; ++s) {  // lengths 128, 64 on a[lane + 32 e]: bits 2, 1 of e
-    const int lr = 4 >> s, m = 4 << s;
-#pragma unroll
-    for (int e = 0; e < 8; ++e)
-      if ((e & lr) == 0) ct_bfly(x[e], x[e + lr], tw1[m + (m >> 2) * Q + e / (2 * lr)], pr);
-  }
-  const int pc = (lane & 7) + 64 * (lane >> 3);  // middle pass: position pc + 8 e
-  __syncwarp();
-#pragma unroll
-  for (int e = 0; e < 8; ++e) xbuf[sw1(lane + 32 * e)] = x[e];
-  __syncwarp();
-#pragma unroll
-  for (int e = 0; e < 8; ++e) x[e] = xbuf[sw1(pc + 8 * e)];
-#pragma unroll
-  for (int s = 0; s < 3; ++s) {  // lengths 32, 16, 8: bits 2 .. 0 of e
-    const int lr = 4 >> s, k0 = (1 << s) - 1;
-#pragma unroll
-    for (int e = 0; e < 8; ++e)
-      if ((e & lr) == 0) ct_bfly(x[e], x[e + lr], zc[k0 + e / (2 * lr)], pr);
-  }
-  __syncwarp();
-#pragma unroll
-  for (int e = 0; e < 8; ++e) xbuf[swp(pc + 8 * e)] = x[e];
-  __syncwarp();
-  const uint4 *xb4 = reinterpret_cast<const uint4 *>(xbuf);
-  const int b = fwd_block8(lane);
-#pragma unroll
-  for (int c = 0; c < 2; ++c) {
-    const uint4 v = xb4[swp(8 * b + 4 * c) >> 2];
-    x[4 * c + 0] = v.x;
-    x[4 * c + 1] = v.y;
-    x[4 * c + 2] = v.z;
-    x[4 * c + 3] = v.w;
-  }
-#pragma unroll
-  for (int s = 0; s < 3; ++s) {  // lengths 4, 2, 1 on a[8 b + e]
-    const int len = 4 >> s, k0 = (1 << s) - 1;
-#pragma unroll
-    for (int e = 0; e < 8; ++e)
-      if ((e & len) == 0) ct_bfly(x[e], x[e + len], zq[k0 + e / (2 * len)], pr);
-  }
-}
-
-// Inverse quarter transform with its per-lane twiddles in registers (zi: middle
-// pass, half-lengths 8, 16, 32, entries of invc; z2: half-lengths 64 and 128,
-// entries 1 .. 6 of inv2), followed by the quarter's share of the output twist
-// (zt[e] = psi^-(c_Q k) at k = lane + 32 e).  In / out as inv_quarter +
-// quarter_twist: x[e] = position 256 Q + 8 lane + e (< 12 q) -> the twisted
-// natural-order result at lane + 32 e (< 2q).
-__device__ __forceinline__ void inv_quarter_r(uint32_t (&x)[8], uint32_t *xbuf, const uint2 *tw1,
-                                              const uint2 (&zi)[7], const uint2 (&z2)[6], const uint2 (&zt)[8],
-                                              const PrimeRT &pr, int lane) {
-#pragma unroll
-  for (int t = 0; t < 3; ++t) {  // half-lengths 1, 2, 4 on a[8 lane + e]
-    const int hh = 1 << t;
-#pragma unroll
-    for (int e = 0; e < 8; ++e)
-      if ((e & hh) == 0) ct_bfly(x[e], x[e + hh], tw1[(hh - 1) + (e & (hh - 1))], pr);
-  }
-  const int pc = (lane & 7) + 64 * (lane >> 3);
-  __syncwarp();
-  uint4 *xb4 = reinterpret_cast<uint4 *>(xbuf);
-#pragma unroll
-  for (int c = 0; c < 2; ++c)
-    xb4[swp(8 * lane + 4 * c) >> 2] = make_uint4(x[4 * c], x[4 * c + 1], x[4 * c + 2], x[4 * c + 3]);
-  __syncwarp();
-#pragma unroll
-  for (int e = 0; e < 8; ++e) x[e] = xbuf[swp(pc + 8 * e)];
-#pragma unroll
-  for (int s = 0; s < 3; ++s) {  // half-lengths 8, 16, 32
-    const int hr = 1 << s;
-#pragma unroll
-    for (int e = 0; e < 8; ++e)
-      if ((e & hr) == 0) ct_bfly(x[e], x[e + hr], zi[(hr - 1) + (e & (hr - 1))], pr);
-  }
-  __syncwarp();
-#pragma unroll
-  for (int e = 0; e < 8; ++e) xbuf[sw1(pc + 8 * e)] = x[e];
-  __syncwarp();
-#pragma unroll
-  for (int e = 0; e < 8; ++e) x[e] = xbuf[sw1(lane + 32 * e)];
-#pragma unroll
-  for (int s = 1; s < 3; ++s) {  // half-lengths 64, 128: entries (hr - 1) + j of inv2, stored from entry 1
-    const int hr = 1 << s;
-#pragma unroll
-    for (int e = 0; e < 8; ++e)
-      if ((e & hr) == 0) ct_bfly(x[e], x[e + hr], z2[(hr - 2) + (e & (hr - 1))], pr);
-  }
-#pragma unroll
-  for (int e = 0; e < 8; ++e) x[e] = shoup_mul(zt[e].x, zt[e].y, x[e], pr.q);
-}
-
 template <int L>
 __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(kThreads, 1)
     br_cluster8_kernel(const __grid_constant__ BrArgs args) {

@@ -80,6 +80,7 @@ int ensure_init(Engine &E) {
     return fail(ARX_ECUDA, "device %s (sm_%d%d): libarx is built for sm_103a", prop.name, prop.major, prop.minor);
   E.sms = prop.multiProcessorCount;
   E.policy.sms = E.sms;
+  E.policy.clusters16 = E.policy.occupancy(BrShape{kCluster16H, 1});
   E.policy.clusters8 = E.policy.occupancy(BrShape{kCluster8H, 1});
   E.policy.clusters4 = E.policy.occupancy(BrShape{kCluster4H, 1});
   E.policy.clusters2 = E.policy.occupancy(BrShape{kClusterH, 1});
@@ -175,7 +176,7 @@ void emit_gate(uint32_t type, uint32_t w0, uint32_t w1, uint32_t w2, uint32_t ou
 // --------------------------------------------------------------------------
 // launch shapes: heuristic and autotuned
 // --------------------------------------------------------------------------
-const BrShape kShapes[] = {{kCluster8H, 1}, {kCluster4H, 1}, {kClusterH, 1}, {6, 1}, {3, 1}, {3, 2}, {2, 1}, {2, 3}, {1, 1}, {1, 2}, {1, 4}, {1, 6}};
+const BrShape kShapes[] = {{kCluster16H, 1}, {kCluster8H, 1}, {kCluster4H, 1}, {kClusterH, 1}, {6, 1}, {3, 1}, {3, 2}, {2, 1}, {2, 3}, {1, 1}, {1, 2}, {1, 4}, {1, 6}};
 
 int ShapePolicy::occupancy(BrShape s) {
   for (auto &kv : occ)
@@ -185,12 +186,13 @@ int ShapePolicy::occupancy(BrShape s) {
   return o;
 }
 
-// Plain mode: an eight-, four-, then two-SM cluster per gate while all of the
+// Plain mode: a sixteen-, eight-, four-, then two-SM cluster per gate while all of the
 // wave's clusters fit on the device at once (larger clusters pack less densely:
 // a cluster must sit in one GPC), then about twelve consumer warps per SM with
 // more gates per CTA as the wave widens.
 BrShape ShapePolicy::heuristic(int jobs) const {
   if (forced.H) return forced;
+  if (jobs <= clusters16) return {kCluster16H, 1};
   if (jobs <= clusters8) return {kCluster8H, 1};
   if (jobs <= clusters4) return {kCluster4H, 1};
   if (jobs <= std::max(clusters2, sms / 2)) return {kClusterH, 1};
@@ -940,7 +942,7 @@ extern "C" int arx_set_launch_shape(int H, int GT) {
     E.policy.forced = BrShape{0, 0};
     return ARX_OK;
   }
-  if (H == kCluster8L2H || !br_shape_supported(BrShape{H, GT}))
+  if (is_l2_shape(BrShape{H, GT}) || !br_shape_supported(BrShape{H, GT}))
     return fail(ARX_EINVAL, "unsupported launch shape (%d, %d)", H, GT);
   E.policy.forced = BrShape{H, GT};
   return ARX_OK;

@@ -66,7 +66,7 @@ struct TuneEntry {
 // serving thread can use a snapshot without the engine lock.
 struct ShapePolicy {
   int sms = 0;
-  int clusters8 = 0, clusters4 = 0, clusters2 = 0;  // co-resident eight- / four- / two-CTA clusters (gates per wave)
+  int clusters16 = 0, clusters8 = 0, clusters4 = 0, clusters2 = 0;  // co-resident 16- / 8- / 4- / 2-CTA clusters
   std::vector<TuneEntry> tune;
   int tuned_n = -1;
   std::vector<std::pair<BrShape, int>> occ;
@@ -74,7 +74,8 @@ struct ShapePolicy {
   int occupancy(BrShape s);
   BrShape heuristic(int jobs) const;
   BrShape pick(int jobs, int n) const;
-  // key sets with gadget l = 2 have one kernel of their own
+  // key sets with gadget l = 2 have one kernel of their own (its four forward
+  // warps already have a scheduler each, so the sixteen-CTA split gains nothing)
   static BrShape for_gadget(int l, BrShape s) { return l == 2 ? BrShape{kCluster8L2H, 1} : s; }
   int grid(BrShape s, int jobs);
 };

@@ -216,6 +216,7 @@ size_t br_smem(BrShape s) {
   if (s.H == kCluster4H) return s.GT == 1 ? br_cluster4_smem() : 0;
   if (s.H == kCluster8H) return s.GT == 1 ? br_cluster8_smem() : 0;
   if (s.H == kCluster8L2H) return s.GT == 1 ? br_cluster8_l2_smem() : 0;
+  if (s.H == kCluster16H) return s.GT == 1 ? br_cluster16_smem() : 0;
   switch (s.H) {
     case 1: return br_smem_h1(s.GT);
     case 2: return br_smem_h2(s.GT);
@@ -232,6 +233,7 @@ int br_occupancy(BrShape s) {
   if (s.H == kCluster4H) return s.GT == 1 ? br_cluster4_occupancy() : 0;
   if (s.H == kCluster8H) return s.GT == 1 ? br_cluster8_occupancy() : 0;
   if (s.H == kCluster8L2H) return s.GT == 1 ? br_cluster8_l2_occupancy() : 0;
+  if (s.H == kCluster16H) return s.GT == 1 ? br_cluster16_occupancy() : 0;
   switch (s.H) {
     case 1: return br_occupancy_h1(s.GT);
     case 2: return br_occupancy_h2(s.GT);
@@ -242,7 +244,7 @@ int br_occupancy(BrShape s) {
 }
 
 int br_threads(BrShape s) {
-  if (s.H == kCluster8H || s.H == kCluster8L2H) return 9 * 32;
+  if (s.H == kCluster8H || s.H == kCluster8L2H || s.H == kCluster16H) return 9 * 32;
   return is_cluster_shape(s) ? 13 * 32 : 2 * s.H * s.GT * 32;
 }
 
@@ -252,6 +254,7 @@ cudaError_t launch_br(const BrArgs &args, BrShape s, int grid, cudaStream_t st) 
   if (s.H == kCluster4H) return s.GT == 1 ? launch_br_cluster4(args, grid, st) : cudaErrorInvalidValue;
   if (s.H == kCluster8H) return s.GT == 1 ? launch_br_cluster8(args, grid, st) : cudaErrorInvalidValue;
   if (s.H == kCluster8L2H) return s.GT == 1 ? launch_br_cluster8_l2(args, grid, st) : cudaErrorInvalidValue;
+  if (s.H == kCluster16H) return s.GT == 1 ? launch_br_cluster16(args, grid, st) : cudaErrorInvalidValue;
   switch (s.H) {
     case 1: return launch_br_h1(args, s.GT, grid, st);
     case 2: return launch_br_h2(args, s.GT, grid, st);

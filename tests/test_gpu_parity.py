@@ -15,7 +15,7 @@ from paper_2306_11006_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
 
-SHAPES = [(48, 1), (24, 1), (12, 1), (6, 1), (3, 1), (3, 2), (2, 1), (2, 3), (1, 1), (1, 2), (1, 4), (1, 6)]
+SHAPES = [(96, 1), (48, 1), (24, 1), (12, 1), (6, 1), (3, 1), (3, 2), (2, 1), (2, 3), (1, 1), (1, 2), (1, 4), (1, 6)]
 
 
 @pytest.fixture(scope="session")
@@ -253,10 +253,10 @@ def test_plan_shapes_report_every_wave(gpu630):
         sh = p.shapes()
         assert len(sh) == p.waves == depth
         assert sum(j for _, _, j in sh) == p.bootstraps
-        # narrow waves take the cluster kernels under the heuristic, the eight-CTA
-        # one for the narrowest (8 clusters of eight CTAs always fit on a GB300)
-        assert all((H, GT) == (48, 1) for H, GT, j in sh if 0 < j <= 8)
-        assert all(H in (12, 24, 48) and GT == 1 for H, GT, j in sh if 0 < j <= arx.device_sms() // 2)
+        # narrow waves take the cluster kernels under the heuristic, the sixteen-
+        # or eight-CTA one for the narrowest (8 clusters of eight CTAs always fit)
+        assert all(H in (96, 48) and GT == 1 for H, GT, j in sh if 0 < j <= 8)
+        assert all(H in (12, 24, 48, 96) and GT == 1 for H, GT, j in sh if 0 < j <= arx.device_sms() // 2)
     arx.set_launch_shape(6, 1)
     try:
         with arx.Plan(nl, mode=arx.MODE_PLAIN) as p:
