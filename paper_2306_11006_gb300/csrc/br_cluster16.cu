@@ -8,9 +8,10 @@
 // the eight-CTA kernel's work split once more, by prime, so that each of a
 // CTA's forward warps has a scheduler of its own.
 //
-// Per CMux: L forward warps (one per row) take the first two forward stages on
-// the packed digit load and run the quarter-Q transform of their row in prime
-// P; each adds its key products for output 1-h into CTA (1-h, Q, P)'s receive
+// Per CMux: all warps compute the gadget digits of the CTA's three rows and
+// take the first two forward stages of quarter Q in prime P at once
+// (make_stage2); three forward warps (one per row) run the rest of the quarter-Q
+// transform of their row; each adds its key products for output 1-h into CTA (1-h, Q, P)'s receive
 // slot with a bulk reduction (1 KiB) and keeps those for output h.  The inverse
 // warp sums the L local rows and the slot (quarter Q of output h in prime P),
 // runs the inverse quarter transform (all stages but the last two, then the
@@ -18,10 +19,10 @@
 // (h, Q', P') (1 KiB each).  All eight CTAs of component h then fold the last
 // two stages, run the CRT and update identical copies of ACC_h.  Every
 // cross-CTA dependency is a transaction count on an mbarrier (double-buffered
-// by CMux parity); every wait is bounded.  Template on the gadget length L, as
-// the eight-CTA kernel, but built for L = 3 only: with L = 2 the eight-CTA
-// kernel's four forward warps already have a scheduler each, and the extra
-// exchange partners made this split slower there (measured).
+// by CMux parity); every wait is bounded.  For the default gadget (l = 3,
+// Bg = 2^7) only: with l = 2 the eight-CTA kernel's four forward warps already
+// have a scheduler each, and the extra exchange partners made this split slower
+// there (measured).
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -34,7 +35,8 @@ namespace brc16 {
 using namespace clu;
 
 constexpr int kClusterSize = 16;
-constexpr int kCons = 8;                    // L forward warps, the inverse warp, helpers for digits and CRT
+constexpr int L = 3;                        // TGSW rows per accumulator component (gadget l = 3)
+constexpr int kCons = 8;                    // three forward warps, the inverse warp, helpers for digits and CRT
 constexpr int kInvWarp = 3;                 // a scheduler of its own
 constexpr int kThreads = (kCons + 1) * 32;  // + producer warp
 constexpr int kConsThreads = kCons * 32;    // 256
@@ -45,12 +47,11 @@ constexpr int kAbarPitch = 640;
 constexpr int kQuarter = 256;
 constexpr uint32_t kPartnerBytes = 7 * kQuarter * 4;  // seven partners, one quarter each
 
-template <int L>
 struct Cfg {
   static constexpr uint32_t kPeerBytes = L * kQuarter * 4;         // the peer's L row products
   static constexpr size_t kRingBytes = (size_t)kStages * kRowBytes;
   static constexpr size_t kAccBytes = kN * 4;
-  static constexpr size_t kDigBytes = (L == 3 ? 3 * 256 : 4 * 256) * 4;
+  static constexpr size_t kDigBytes = (size_t)L * 256 * 4;        // [row][k] stage-2 values of quarter Q
   static constexpr size_t kOwnBytes = (size_t)L * kQuarter * 4;       // [row][quarter Q] products for output h
   static constexpr size_t kOthBytes = (size_t)2 * L * kQuarter * 4;   // [parity][row] for output 1-h
   static constexpr size_t kSlotBytes = (size_t)2 * kQuarter * 4;      // [parity] the peer's row sum
@@ -62,13 +63,12 @@ struct Cfg {
                                   kPostBytes + kScrBytes + kAbarBytes + kBarBytes;
 };
 
-template <int L>
 __global__ void __launch_bounds__(kThreads, 1) br_cluster16_kernel(const __grid_constant__ BrArgs args) {
-  using C = Cfg<L>;
+  using C = Cfg;
   extern __shared__ __align__(128) uint8_t smem[];
   uint32_t *ring = reinterpret_cast<uint32_t *>(smem);  // [stage][output][N]
   uint32_t *A = reinterpret_cast<uint32_t *>(smem + C::kRingBytes);
-  uint32_t *D = A + kN;                          // packed digits
+  uint32_t *D = A + kN;                          // [row][k] stage-2 values (make_stage2)
   uint32_t *own = D + C::kDigBytes / 4;          // [row][256], swizzled (swp)
   uint32_t *oth = own + L * kQuarter;            // [parity][row][256], same layout
   uint32_t *slots = oth + 2 * L * kQuarter;      // [parity][256], same layout, zero between uses
@@ -141,15 +141,13 @@ __global__ void __launch_bounds__(kThreads, 1) br_cluster16_kernel(const __grid_
     const bool fwd = warp < L;
     const int rr = fwd ? warp : 0;  // forward warps: row L h + rr
     const int tid = threadIdx.x;    // 0 .. 255
-    PrimeRT pr = prime_rt(P, args.tc);
-    if (L == 2) {  // first-stage offsets of 10-bit digits
-      pr.dc = args.tc.dig_c2[P];
-      pr.dd = args.tc.dig_d2[P];
-    }
+    const PrimeRT pr = prime_rt(P, args.tc);
     uint32_t *myscr = scratch + warp * kQuarter;
     const uint2 *tw1f = args.tc.fwd1[P], *tw1i = args.tc.inv1[P];
     const uint2 z1 = args.tc.fwd1[P][1], z23 = args.tc.fwd1[P][2 + (Q >> 1)];
     const int fb = fwd_block8(lane);
+    const PrimeRT prs[1] = {pr};
+    const uint2 z1s[1] = {z1}, z23s[1] = {z23};
     // loop-invariant per-lane twiddles
     uint2 zc[7], zq[7], zi[7], z2[6], zt[8];
 #pragma unroll
@@ -178,17 +176,12 @@ __global__ void __launch_bounds__(kThreads, 1) br_cluster16_kernel(const __grid_
 
       for (int i = 0; i < n; ++i, ++cm) {
         const uint32_t par = cm & 1u, ph = (cm >> 1) & 1u;
-        if (L == 3)
-          make_digits4(D, A, abar[i], tid, kConsThreads);
-        else
-          make_digits_l2(D, A, abar[i], tid, kConsThreads);
+        make_stage2<L, 1>(D, A, abar[i], z1s, z23s, Q, prs, tid, kConsThreads);
         named_bar(1, kConsThreads);
         if (fwd) {
           uint32_t x[8];
-          if (L == 3)
-            load_first2(x, D + rr * 256, z1, z23, Q, pr, lane);
-          else
-            load_first2_l2(x, D + rr * 512, z1, z23, Q, pr, lane);
+#pragma unroll
+          for (int e = 0; e < 8; ++e) x[e] = D[rr * 256 + lane + 32 * e];
           fwd_quarter_r(x, myscr, tw1f, zc, zq, Q, pr, lane);
           const uint32_t jc = (it * (uint32_t)n + (uint32_t)i) * (uint32_t)L + (uint32_t)rr;
           const uint32_t slot = jc % kStages;
@@ -289,24 +282,22 @@ __global__ void __launch_bounds__(kThreads, 1) br_cluster16_kernel(const __grid_
 }  // namespace brc16
 
 namespace {
-template <int L>
 cudaError_t prepare16() {
   static bool attr = false;  // calls are serialised by the engine lock
   if (attr) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(brc16::br_cluster16_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)brc16::Cfg<L>::kSmem);
+  cudaError_t e = cudaFuncSetAttribute(brc16::br_cluster16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)brc16::Cfg::kSmem);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(brc16::br_cluster16_kernel<L>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    e = cudaFuncSetAttribute(brc16::br_cluster16_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e == cudaSuccess) attr = true;
   return e;
 }
 
-template <int L>
 cudaLaunchConfig_t config16(int clusters, cudaStream_t st, cudaLaunchAttribute *at) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(brc16::kClusterSize * clusters, 1, 1);
   cfg.blockDim = dim3(brc16::kThreads, 1, 1);
-  cfg.dynamicSmemBytes = brc16::Cfg<L>::kSmem;
+  cfg.dynamicSmemBytes = brc16::Cfg::kSmem;
   cfg.stream = st;
   at->id = cudaLaunchAttributeClusterDimension;
   at->val.clusterDim.x = brc16::kClusterSize;
@@ -317,26 +308,24 @@ cudaLaunchConfig_t config16(int clusters, cudaStream_t st, cudaLaunchAttribute *
   return cfg;
 }
 
-template <int L>
 cudaError_t launch16(const BrArgs &args, int clusters, cudaStream_t st) {
-  cudaError_t e = prepare16<L>();
+  cudaError_t e = prepare16();
   if (e != cudaSuccess) return e;
   cudaLaunchAttribute at;
-  cudaLaunchConfig_t cfg = config16<L>(clusters, st, &at);
-  return cudaLaunchKernelEx(&cfg, brc16::br_cluster16_kernel<L>, args);
+  cudaLaunchConfig_t cfg = config16(clusters, st, &at);
+  return cudaLaunchKernelEx(&cfg, brc16::br_cluster16_kernel, args);
 }
 
 // Co-resident sixteen-CTA clusters (0 where the device does not allow them).
-template <int L>
 int occupancy16() {
-  if (prepare16<L>() != cudaSuccess) {
+  if (prepare16() != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
   cudaLaunchAttribute at;
-  cudaLaunchConfig_t cfg = config16<L>(1, nullptr, &at);
+  cudaLaunchConfig_t cfg = config16(1, nullptr, &at);
   int clusters = 0;
-  if (cudaOccupancyMaxActiveClusters(&clusters, brc16::br_cluster16_kernel<L>, &cfg) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveClusters(&clusters, brc16::br_cluster16_kernel, &cfg) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
@@ -344,10 +333,10 @@ int occupancy16() {
 }
 }  // namespace
 
-size_t br_cluster16_smem() { return brc16::Cfg<3>::kSmem; }
+size_t br_cluster16_smem() { return brc16::Cfg::kSmem; }
 cudaError_t launch_br_cluster16(const BrArgs &args, int clusters, cudaStream_t st) {
-  return launch16<3>(args, clusters, st);
+  return launch16(args, clusters, st);
 }
-int br_cluster16_occupancy() { return occupancy16<3>(); }
+int br_cluster16_occupancy() { return occupancy16(); }
 
 }  // namespace arx

@@ -6,9 +6,11 @@
 // 2 Q + h) owns accumulator component ACC_h, the three TGSW rows whose digits
 // come from it (rows 3h .. 3h+2), and spectral quarter Q, for both CRT primes.
 //
-// Per CMux: six forward warps (row, prime) take the first two forward stages on
-// the packed digit load and run the quarter-Q transform of their row (the
-// quarters of a negacyclic transform are independent after those two stages).
+// Per CMux: all warps compute the gadget digits of the CTA's rows and take the
+// first two forward stages of quarter Q in both primes at once (make_stage2:
+// the quarters of a negacyclic transform are independent after those two
+// stages); six forward warps (row, prime) run the rest of their quarter-Q
+// transform.
 // Each adds its key products for output 1-h into CTA (1-h, Q)'s receive slot
 // with a bulk reduction (1 KiB).  With the products it receives, the CTA holds
 // quarter Q of both primes' sums of output h; two warps run the two inverse
@@ -47,7 +49,7 @@ struct Cfg {
   // shared memory (bytes)
   static constexpr size_t kRingBytes = (size_t)kStages * kChunkBytes;
   static constexpr size_t kAccBytes = kN * 4;                     // ACC_h
-  static constexpr size_t kDigBytes = (L == 3 ? 3 * 256 : 4 * 256) * 4;  // packed digits (see make_digits*)
+  static constexpr size_t kDigBytes = (size_t)2 * L * 256 * 4;    // [prime][row][k] stage-2 values (make_stage2)
   static constexpr size_t kOwnBytes = 2 * L * kQuarter * 4;       // [prime][row][quarter Q] products for output h
   static constexpr size_t kOthBytes = 2 * 2 * L * kQuarter * 4;   // [parity][prime][row][quarter Q] for output 1-h
   static constexpr size_t kSlotBytes = 2 * 2 * kQuarter * 4;      // [parity][prime][quarter Q] the peer's row sums
@@ -67,7 +69,7 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(kThreads, 1)
   extern __shared__ __align__(128) uint8_t smem[];
   uint32_t *ring = reinterpret_cast<uint32_t *>(smem);
   uint32_t *A = reinterpret_cast<uint32_t *>(smem + C::kRingBytes);
-  uint32_t *D = A + kN;                          // packed digits
+  uint32_t *D = A + kN;                          // [prime][row][k] stage-2 values
   uint32_t *own = D + C::kDigBytes / 4;          // [prime][row][256], swizzled (swp)
   uint32_t *oth = own + 2 * L * kQuarter;        // [parity][prime][row][256], same layout
   uint32_t *slots = oth + 4 * L * kQuarter;      // [parity][prime][256], same layout, zero between uses
@@ -137,14 +139,19 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(kThreads, 1)
     const bool fwd = warp < kFwd;
     const int rr = fwd ? warp >> 1 : 0, P = warp & 1;  // forward warps: row L h + rr, prime P
     const int tid = threadIdx.x;                         // 0 .. 255
-    PrimeRT pr = prime_rt(P, args.tc);
+    const PrimeRT pr = prime_rt(P, args.tc);
+    PrimeRT prs[2] = {prime_rt(0, args.tc), prime_rt(1, args.tc)};
     if (L == 2) {  // first-stage offsets of 10-bit digits
-      pr.dc = args.tc.dig_c2[P];
-      pr.dd = args.tc.dig_d2[P];
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {
+        prs[p].dc = args.tc.dig_c2[p];
+        prs[p].dd = args.tc.dig_d2[p];
+      }
     }
+    const uint2 z1s[2] = {args.tc.fwd1[0][1], args.tc.fwd1[1][1]};
+    const uint2 z23s[2] = {args.tc.fwd1[0][2 + (Q >> 1)], args.tc.fwd1[1][2 + (Q >> 1)]};
     uint32_t *myscr = scratch + (fwd ? warp : 0) * kQuarter;
     const uint2 *tw1f = args.tc.fwd1[P], *tw1i = args.tc.inv1[P];
-    const uint2 z1 = args.tc.fwd1[P][1], z23 = args.tc.fwd1[P][2 + (Q >> 1)];
     const int fb = fwd_block8(lane);
     // loop-invariant per-lane twiddles
     uint2 zc[7], zq[7], zi[7], z2[6], zt[8];
@@ -174,17 +181,12 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(kThreads, 1)
 
       for (int i = 0; i < n; ++i, ++cm) {
         const uint32_t par = cm & 1u, ph = (cm >> 1) & 1u;
-        if (L == 3)
-          make_digits4(D, A, abar[i], tid, kConsThreads);
-        else
-          make_digits_l2(D, A, abar[i], tid, kConsThreads);
+        make_stage2<L, 2>(D, A, abar[i], z1s, z23s, Q, prs, tid, kConsThreads);
         named_bar(1, kConsThreads);
         if (fwd) {
           uint32_t x[8];
-          if (L == 3)
-            load_first2(x, D + rr * 256, z1, z23, Q, pr, lane);
-          else
-            load_first2_l2(x, D + rr * 512, z1, z23, Q, pr, lane);
+#pragma unroll
+          for (int e = 0; e < 8; ++e) x[e] = D[(P * L + rr) * 256 + lane + 32 * e];
           fwd_quarter_r(x, myscr, tw1f, zc, zq, Q, pr, lane);
           const uint32_t jc = (it * (uint32_t)n + (uint32_t)i) * (uint32_t)L + (uint32_t)rr;
           const uint32_t slot = jc % kStages;

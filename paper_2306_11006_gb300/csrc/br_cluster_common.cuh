@@ -102,10 +102,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
   return ok != 0;
 }
 
+// Bounded wait: a phase that has already completed returns at once (the abort
+// flag is read only on the slow path, where a wait could otherwise last);
+// returns false (and flags the CTA and the device status) on timeout.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
                                           unsigned int *status) {
-  if (*abort_flag) return false;
   if (mbar_try_wait(bar, parity)) return true;
+  if (*abort_flag) return false;
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
     if (*abort_flag) return false;
@@ -283,47 +286,9 @@ __device__ __forceinline__ void make_digits4(uint32_t *D, const uint32_t *A, uin
   }
 }
 
-// The same for the gadget variant l = 2, Bg = 2^10 (10-bit digits): rounding
-// half of the 20-bit gadget plus the +512 offset of each digit; D[r][0][k] holds
-// the digits u = d + 512 of positions k and k+256 (16-bit halves), D[r][1][k]
-// those of k+512 and k+768.
+// Rounding half of the 20-bit gadget of the variant l = 2, Bg = 2^10, plus the
+// +512 offset of each 10-bit digit.
 constexpr uint32_t kDecOffset2 = (1u << 11) + (512u << 22) + (512u << 12);
-__device__ __forceinline__ void make_digits_l2(uint32_t *D, const uint32_t *A, uint32_t a, int tid, int nthreads) {
-  for (int k = tid; k < 256; k += nthreads) {
-    uint32_t u0[4], u1[4];  // rows 0, 1 at position k + 256 m
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      const uint32_t pos = (uint32_t)k + 256u * m;
-      const uint32_t j = (pos - a) & 2047u;
-      uint32_t v = A[j & 1023u];
-      v = (j & 1024u) ? 0u - v : v;
-      const uint32_t y = v - A[pos] + kDecOffset2;
-      u0[m] = y >> 22;
-      u1[m] = (y >> 12) & 0x3FFu;
-    }
-    D[k] = u0[0] | (u0[1] << 16);
-    D[256 + k] = u0[2] | (u0[3] << 16);
-    D[512 + k] = u1[0] | (u1[1] << 16);
-    D[768 + k] = u1[2] | (u1[3] << 16);
-  }
-}
-
-// load_first2 for 10-bit digits (rows packed by make_digits_l2; Dr = one row).
-// Out < 5q + 1024.
-__device__ __forceinline__ void load_first2_l2(uint32_t (&x)[8], const uint32_t *Dr, uint2 z1, uint2 z23, int Qf,
-                                               const PrimeRT &pr, int lane) {
-#pragma unroll
-  for (int e = 0; e < 8; ++e) {
-    const uint32_t d01 = Dr[lane + 32 * e], d23 = Dr[256 + lane + 32 * e];
-    const uint32_t t0 = shoup_mul(z1.x, z1.y, d23 & 0xFFFFu, pr.q);
-    const uint32_t t1 = shoup_mul(z1.x, z1.y, d23 >> 16, pr.q);
-    const uint32_t u0 = d01 & 0xFFFFu, u1 = d01 >> 16;
-    const uint32_t a = Qf < 2 ? u0 + t0 + pr.dc : u0 - t0 + pr.q2 + pr.dd;
-    const uint32_t b = Qf < 2 ? u1 + t1 + pr.dc : u1 - t1 + pr.q2 + pr.dd;
-    const uint32_t t2 = shoup_mul(z23.x, z23.y, b, pr.q);
-    x[e] = (Qf & 1) ? a - t2 + pr.q2 : a + t2;
-  }
-}
 
 // Forward quarter transform with its per-lane twiddles in registers (zc: middle
 // pass, lengths 32, 16, 8; zq: last pass, lengths 4, 2, 1; same entries as the
@@ -424,6 +389,55 @@ __device__ __forceinline__ void inv_quarter_r(uint32_t (&x)[8], uint32_t *xbuf, 
   }
 #pragma unroll
   for (int e = 0; e < 8; ++e) x[e] = shoup_mul(zt[e].x, zt[e].y, x[e], pr.q);
+}
+
+// Gadget digits of X^a ACC - ACC (Fig. 2) with the first two forward stages
+// (distances 512 and 256) of spectral quarter Qf taken at once, for each of NP
+// primes: S[p][r][k] = the stage-2 output at position k of quarter Qf for row r
+// in prime p (< 5q + 2^bits), from the digits u = d + 2^(bits-1) at k, k + 256,
+// k + 512, k + 768 (the offsets ride on pr[p].dc, pr[p].dd).  L = 3: 7-bit
+// digits (Bg = 2^7); L = 2: 10-bit digits (Bg = 2^10).  Run by all of a CTA's
+// threads, it takes these stages off the forward warps' path (for L = 3 the
+// values are those make_digits4 and load_first2 give).
+template <int L, int NP>
+__device__ __forceinline__ void make_stage2(uint32_t *S, const uint32_t *A, uint32_t a, const uint2 (&z1)[NP],
+                                            const uint2 (&z23)[NP], int Qf, const PrimeRT (&pr)[NP], int tid,
+                                            int nthreads) {
+  static_assert(L == 2 || L == 3, "gadget length");
+  for (int k = tid; k < 256; k += nthreads) {
+    uint32_t u[4][L];  // u[m][r]: digit + offset of row r at position k + 256 m
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const uint32_t pos = (uint32_t)k + 256u * m;
+      const uint32_t j = (pos - a) & 2047u;
+      uint32_t v = A[j & 1023u];
+      v = (j & 1024u) ? 0u - v : v;
+      if constexpr (L == 3) {
+        const uint32_t y = v - A[pos] + kDecOffset;
+        u[m][0] = y >> 25;
+        u[m][1] = (y >> 18) & 0x7Fu;
+        u[m][2] = (y >> 11) & 0x7Fu;
+      } else {
+        const uint32_t y = v - A[pos] + kDecOffset2;
+        u[m][0] = y >> 22;
+        u[m][1] = (y >> 12) & 0x3FFu;
+      }
+    }
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+#pragma unroll
+      for (int r = 0; r < L; ++r) {
+        const uint32_t t0 = shoup_mul(z1[p].x, z1[p].y, u[2][r], pr[p].q);
+        const uint32_t t1 = shoup_mul(z1[p].x, z1[p].y, u[3][r], pr[p].q);
+        // stage 1 (distance 512): the upper spectral half takes the differences
+        const uint32_t s0 = Qf < 2 ? u[0][r] + t0 + pr[p].dc : u[0][r] - t0 + pr[p].q2 + pr[p].dd;
+        const uint32_t s1 = Qf < 2 ? u[1][r] + t1 + pr[p].dc : u[1][r] - t1 + pr[p].q2 + pr[p].dd;
+        // stage 2 (distance 256) with zeta[2] or zeta[3]
+        const uint32_t t2 = shoup_mul(z23[p].x, z23[p].y, s1, pr[p].q);
+        S[(p * L + r) * 256 + k] = (Qf & 1) ? s0 - t2 + pr[p].q2 : s0 + t2;
+      }
+    }
+  }
 }
 
 // Last two inverse stages and CRT of both primes, then ACC += the Torus32
