@@ -150,7 +150,7 @@ __device__ __forceinline__ void ntt_fwd(uint32_t (&x)[32], uint32_t *xbuf, const
 }
 
 // Inverse (the 1/N factor rides on the stored key): x[e] = A[32 lane + e] < 12 q
-// -> x[e] = a[lane + 32 e] in [0, q).
+// -> x[e] = a[lane + 32 e] in [0, 2q) (what crt_torus takes).
 __device__ __forceinline__ void ntt_inv(uint32_t (&x)[32], uint32_t *xbuf, const uint2 *tw1,
                                         const uint2 *__restrict__ tw2, const uint2 *__restrict__ twist,
                                         const PrimeRT &pr, int lane) {
@@ -181,7 +181,7 @@ __device__ __forceinline__ void ntt_inv(uint32_t (&x)[32], uint32_t *xbuf, const
 #pragma unroll
   for (int e = 0; e < 32; ++e) {
     const uint2 w = __ldg(twist + e * 32 + lane);
-    x[e] = csub(shoup_mul(w.x, w.y, x[e], pr.q), pr.q);
+    x[e] = shoup_mul(w.x, w.y, x[e], pr.q);
   }
 }
 

@@ -139,8 +139,10 @@ __device__ __forceinline__ void named_bar(int id, int threads) {
 
 __device__ __forceinline__ uint32_t modswitch(uint32_t x) { return (x + (1u << 20)) >> 21; }
 
+// Garner recombination of (x0 mod q0, x1 mod q1), each in [0, 2q), to the
+// centred integer mod 2^32 (the reasoning is at br::crt_torus).
 __device__ __forceinline__ uint32_t crt_torus(uint32_t x0, uint32_t x1) {
-  const uint32_t d = x1 + 2u * kQ1 - x0;
+  const uint32_t d = x1 + 3u * kQ1 - x0;
   const uint32_t k = csub(shoup_mul(kQ0InvQ1, kQ0InvQ1Shoup, d, kQ1), kQ1);
   const uint32_t r = kQ0 * k + x0;
   return k >= kQ1 / 2 ? r - (uint32_t)kM : r;
@@ -249,18 +251,19 @@ __device__ __forceinline__ void quarter_twist(uint32_t (&x)[8], const uint2 *__r
   }
 }
 
-// Last two inverse stages, output twist and full reduction for one prime:
-// outputs k, k + 256, k + 512, k + 768 from the twisted quarter outputs
-// t = (psi^-k u_0, psi^-5k u_1, psi^-3k u_2, psi^-7k u_3) at k, each in [0, 2q).
+// Last two inverse stages and the output twist for one prime: outputs k,
+// k + 256, k + 512, k + 768 (each in [0, 2q), what crt_torus takes) from the
+// twisted quarter outputs t = (psi^-k u_0, psi^-5k u_1, psi^-3k u_2,
+// psi^-7k u_3) at k, each in [0, 2q).
 __device__ __forceinline__ void inv_last(uint32_t (&o)[4], const uint32_t (&t)[4], uint2 m512, uint2 m256,
                                          uint32_t q) {
   const uint32_t s01 = t[0] + t[1], d01 = t[0] - t[1] + 2u * q;  // < 4q
   const uint32_t s23 = t[2] + t[3], d23 = t[2] - t[3] + 2u * q;
-  o[0] = csub(csub(csub(s01 + s23, 4u * q), 2u * q), q);
-  o[2] = csub(shoup_mul(m512.x, m512.y, s01 - s23 + 4u * q, q), q);
+  o[0] = csub(csub(s01 + s23, 4u * q), 2u * q);
+  o[2] = shoup_mul(m512.x, m512.y, s01 - s23 + 4u * q, q);
   const uint32_t e23 = shoup_mul(m512.x, m512.y, d23, q), e01 = shoup_mul(m512.x, m512.y, d01, q);
-  o[1] = csub(shoup_mul(m256.x, m256.y, d01 + e23, q), q);
-  o[3] = csub(shoup_mul(m256.x, m256.y, e01 + d23, q), q);
+  o[1] = shoup_mul(m256.x, m256.y, d01 + e23, q);
+  o[3] = shoup_mul(m256.x, m256.y, e01 + d23, q);
 }
 
 // Gadget digits of X^a ACC - ACC (Fig. 2), packed for the split forward

@@ -38,7 +38,7 @@ constexpr uint32_t kQ0InvQ1 = pow_mod(kQ0, kQ1 - 2, kQ1);
 constexpr uint32_t kQ0InvQ1Shoup = (uint32_t)(((uint64_t)kQ0InvQ1 << 32) / kQ1);
 constexpr uint64_t kM = (uint64_t)kQ0 * kQ1;
 static_assert(32ull * kQ0 < (1ull << 32) && 32ull * kQ1 < (1ull << 32), "lazy transform bounds");
-static_assert(kQ0 > kQ1 && kQ0 < 2ull * kQ1, "CRT difference stays positive");
+static_assert(2ull * kQ0 < 3ull * kQ1 && 5ull * kQ1 < (1ull << 32), "CRT difference stays in (0, 2^32)");
 static_assert(6ull * 1024 * 64 * (1ull << 31) * 2 < kM / 4, "CRT range must hold the exact products");
 
 // Gadget decomposition offset: 2^10 rounds to the top 21 bits, 64 * 2^(32-7p)
@@ -107,11 +107,15 @@ __device__ __forceinline__ void named_bar(int id, int threads) {
 
 __device__ __forceinline__ uint32_t modswitch(uint32_t x) { return (x + (1u << 20)) >> 21; }
 
-// (x0 mod q0, x1 mod q1), both fully reduced -> the centred integer, mod 2^32.
-// Garner: X = x0 + q0 k, k = (x1 - x0) q0^-1 mod q1.  The exact value is below
-// 2^50 in magnitude, so it is negative exactly when k >= q1 / 2.
+// (x0 mod q0, x1 mod q1), each in [0, 2q) -> the centred integer V, mod 2^32.
+// Garner: X = x0 + q0 k, k = (x1 - x0) q0^-1 mod q1 fully reduced (d stays in
+// (0, 2^32) for these input ranges).  |V| < 2^50, so the coefficient K of V's
+// representative in [0, q0 q1) is below 2^23 (V >= 0) or above q1 - 2^23
+// (V < 0): V is negative exactly when k >= q1 / 2, and then X - q0 q1 = V.  An
+// x0 one q0 above its residue gives k = K - 1; for K = 0 (0 <= V < q0) that
+// wraps to q1 - 1, X = V + q0 q1, and the same rule returns V.
 __device__ __forceinline__ uint32_t crt_torus(uint32_t x0, uint32_t x1) {
-  const uint32_t d = x1 + 2u * kQ1 - x0;
+  const uint32_t d = x1 + 3u * kQ1 - x0;
   const uint32_t k = csub(shoup_mul(kQ0InvQ1, kQ0InvQ1Shoup, d, kQ1), kQ1);
   const uint32_t r = kQ0 * k + x0;
   return k >= kQ1 / 2 ? r - (uint32_t)kM : r;
