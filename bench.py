@@ -52,12 +52,16 @@ def modmul_per_cmux(l: int = 3) -> int:
 
 
 MODMUL_PER_CMUX = modmul_per_cmux(3)
-# integer-ALU peak: 152 SMs x 2070 MHz x 64 IMAD lanes/clk / 3 IMADs per Shoup or
-# Montgomery modular multiply (derivation in the design doc)
+# integer-ALU peak: 152 SMs x 2070 MHz x 64 IMAD-capable lanes per clock, a
+# Shoup or Montgomery modular multiply taking 3 of those lane slots
 ALU_PEAK_TMODMUL = 152 * 2.070e9 * 64 / 3 / 1e12
 # DRAM bytes (read + write) per launch from one ncu capture of the current kernel
 # build (profiles/): the key once per launch.  Only kernels listed here report it.
-TRAFFIC_PER_LAUNCH = {"br_cluster8_kernel": 62.09e6 + 0.07e6}
+TRAFFIC_PER_LAUNCH = {
+    "br_cluster16_kernel": 62.06e6 + 2.69e6,  # 7 gates
+    "br_cluster8_kernel": 62.06e6 + 2.08e6,   # 8 gates
+    "br_kernel<1,6>": 66.84e6 + 2.66e6,       # 912 gates
+}
 
 
 def replica_max_ms(ms: float, world: int, device="cpu") -> float:
