@@ -146,13 +146,17 @@ int br_cluster16_occupancy();
 inline bool is_cluster_shape(BrShape s) {
   return s.H == kClusterH || s.H == kCluster4H || s.H == kCluster8H || s.H == kCluster8L2H || s.H == kCluster16H;
 }
+// Shapes {kGadget2 + H, GT}: the throughput kernel br_kernel<H, GT, 2> for key
+// sets with gadget l = 2 (H in 1, 2, 4).
+constexpr int kGadget2 = 100;
 // Shapes reserved for key sets with gadget l = 2 (never an override).
-inline bool is_l2_shape(BrShape s) { return s.H == kCluster8L2H; }
+inline bool is_l2_shape(BrShape s) { return s.H == kCluster8L2H || s.H > kGadget2; }
 
 // per-shape launchers (one translation unit per H)
-cudaError_t launch_br_h1(const BrArgs &args, int GT, int grid, cudaStream_t st);
-cudaError_t launch_br_h2(const BrArgs &args, int GT, int grid, cudaStream_t st);
-cudaError_t launch_br_h3(const BrArgs &args, int GT, int grid, cudaStream_t st);
-cudaError_t launch_br_h6(const BrArgs &args, int GT, int grid, cudaStream_t st);
+cudaError_t launch_br_h1(const BrArgs &args, int GT, int L, int grid, cudaStream_t st);
+cudaError_t launch_br_h2(const BrArgs &args, int GT, int L, int grid, cudaStream_t st);
+cudaError_t launch_br_h3(const BrArgs &args, int GT, int L, int grid, cudaStream_t st);
+cudaError_t launch_br_h4(const BrArgs &args, int GT, int L, int grid, cudaStream_t st);
+cudaError_t launch_br_h6(const BrArgs &args, int GT, int L, int grid, cudaStream_t st);
 
 }  // namespace arx

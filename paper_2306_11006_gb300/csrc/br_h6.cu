@@ -1,25 +1,34 @@
-// br_h6.cu -- blind-rotation kernel shapes with H = 6 (2H warps per gate).
+// br_h6.cu -- blind-rotation kernel shapes with H = 6 (2H warps per gate); gadget length L = 3.
 #include "br_kernel.cuh"
 
 namespace arx {
 
-cudaError_t launch_br_h6(const BrArgs &args, int GT, int grid, cudaStream_t st) {
+cudaError_t launch_br_h6(const BrArgs &args, int GT, int L, int grid, cudaStream_t st) {
+  if (L == 2) {
+    return cudaErrorInvalidValue;
+  }
   switch (GT) {
-    case 1: return br::launch_shape<6, 1>(args, grid, st);
+    case 1: return br::launch_shape<6, 1, 3>(args, grid, st);
     default: return cudaErrorInvalidValue;
   }
 }
 
-size_t br_smem_h6(int GT) {
+size_t br_smem_h6(int GT, int L) {
+  if (L == 2) {
+    return 0;
+  }
   switch (GT) {
     case 1: return br::br_smem_bytes<6, 1>();
     default: return 0;
   }
 }
 
-int br_occupancy_h6(int GT) {
+int br_occupancy_h6(int GT, int L) {
+  if (L == 2) {
+    return 0;
+  }
   switch (GT) {
-    case 1: return br::occupancy_shape<6, 1>();
+    case 1: return br::occupancy_shape<6, 1, 3>();
     default: return 0;
   }
 }

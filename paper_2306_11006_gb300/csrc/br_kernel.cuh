@@ -1,11 +1,12 @@
 // br_kernel.cuh -- the blind-rotation kernel of CGGI gate bootstrapping on GB300.
 //
-//   br_kernel<H, GT>: gate pre-combination, mod switch, blind rotation through n
+//   br_kernel<H, GT, L>: gate pre-combination, mod switch, blind rotation through n
 //   CMux external products, sample extraction (Fig. 2 and Sec. 2.2 of the paper).
 //   Each br_h*.cu translation unit instantiates the shapes of one H.
 //
 // Blind rotation kernel organisation.  A gate is processed by 2H warps: warp
-// (P, h) carries prime P of the CRT pair and the h-th group of 6/H TGSW rows.
+// (P, h) carries prime P of the CRT pair and the h-th group of 2L/H TGSW rows
+// (gadget length L: 3 for Bg = 2^7, 2 for the paper's own Bg = 2^10).
 // GT gates share a CTA so that every bootstrapping-key row (16 KiB: two output
 // polynomials x two primes) is brought into shared memory once per CTA
 // (cp.async.bulk into a 4..8-stage mbarrier ring) and read by all 2 GT warps that
@@ -44,6 +45,9 @@ static_assert(6ull * 1024 * 64 * (1ull << 31) * 2 < kM / 4, "CRT range must hold
 // Gadget decomposition offset: 2^10 rounds to the top 21 bits, 64 * 2^(32-7p)
 // recentres each 7-bit digit into [-64, 64).
 constexpr uint32_t kDecOffset = (1u << 10) + (64u << 25) + (64u << 18) + (64u << 11);
+// The same for the gadget variant l = 2, Bg = 2^10: 2^11 rounds to the top 20
+// bits, 512 * 2^(32-10p) recentres each 10-bit digit into [-512, 512).
+constexpr uint32_t kDecOffset2 = (1u << 11) + (512u << 22) + (512u << 12);
 
 constexpr long long kWaitCycles = 4000000000ll;  // ~2 s at GB300 clocks
 
@@ -122,9 +126,10 @@ __device__ __forceinline__ uint32_t crt_torus(uint32_t x0, uint32_t x1) {
 }
 
 // Gadget digits of temp = X^a ACC - ACC for both polynomials, computed by the
-// gate's threads into dig[c][k] and packed as three biased 7-bit fields
-// (digit + 64), p = 1 in the low byte.
-template <int kGateThreads>
+// gate's threads into dig[c][k]: for L = 3 three biased 7-bit fields (digit +
+// 64) with p = 1 in the low byte; for L = 2 two biased 10-bit fields (digit +
+// 512) with p = 1 in the low half.
+template <int kGateThreads, int L>
 __device__ __forceinline__ void make_digits(uint32_t *dig, const uint32_t *A, uint32_t a, int tid_g) {
 #pragma unroll 4
   for (int idx = tid_g; idx < 2 * kN; idx += kGateThreads) {
@@ -133,8 +138,13 @@ __device__ __forceinline__ void make_digits(uint32_t *dig, const uint32_t *A, ui
     const uint32_t j = (k - a) & 2047u;
     uint32_t v = P[j & 1023u];
     v = (j & 1024u) ? 0u - v : v;
-    const uint32_t y = v - P[k] + kDecOffset;
-    dig[idx] = (y >> 25) | ((y >> 10) & 0x7F00u) | ((y << 5) & 0x7F0000u);
+    if constexpr (L == 3) {
+      const uint32_t y = v - P[k] + kDecOffset;
+      dig[idx] = (y >> 25) | ((y >> 10) & 0x7F00u) | ((y << 5) & 0x7F0000u);
+    } else {
+      const uint32_t y = v - P[k] + kDecOffset2;
+      dig[idx] = (y >> 22) | (((y >> 12) & 0x3FFu) << 16);
+    }
   }
 }
 
@@ -189,32 +199,34 @@ __device__ __forceinline__ BrShared br_carve(uint8_t *smem) {
   return s;
 }
 
-// Key rows this CTA consumes: 6 n per tile of GT gates.
-template <int GT>
+// Key rows this CTA consumes: 2L n per tile of GT gates (2L TGSW rows per CMux).
+template <int GT, int L>
 __device__ __forceinline__ uint32_t cta_rows(const BrArgs &args) {
   const int tiles = (args.num_jobs + GT - 1) / GT;
   const int mine = (int)blockIdx.x < tiles ? (tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-  return (uint32_t)mine * 6u * (uint32_t)args.n;
+  return (uint32_t)mine * (2u * L) * (uint32_t)args.n;
 }
 
-// Copy key row jc of the CTA's sequence (row jc mod 6n of the key: CMux i,
+// Copy key row jc of the CTA's sequence (row jc mod 2Ln of the key: CMux i,
 // TGSW row r) into its ring slot.
-template <int kStages>
+template <int kStages, int L>
 __device__ __forceinline__ void issue_row(const BrShared &S, const BrArgs &args, uint32_t jc) {
   const uint32_t slot = jc % kStages;
   S.issued[slot] = jc + 1u;
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic reads of the slot before the copy
   mbar_expect_tx(S.full + slot, kChunkBytes);
-  bulk_g2s(S.ring + slot * kChunkWords, args.bsk + (size_t)(jc % (6u * (uint32_t)args.n)) * kChunkWords,
+  bulk_g2s(S.ring + slot * kChunkWords, args.bsk + (size_t)(jc % (2u * L * (uint32_t)args.n)) * kChunkWords,
            kChunkBytes, S.full + slot);
 }
 
 // One warp (prime P, row group h) over all tiles of the launch.  The
 // same code serves both primes; the owner of output c (warp (P, c) for H > 1,
 // both outputs for H = 1) keeps that output's accumulator in acc0.
-template <int H, int GT>
+template <int H, int GT, int L>
 __device__ __forceinline__ void br_consumer(const BrShared &S, const BrArgs &args, int g, int h, int P, int lane) {
-  constexpr int kRpg = 6 / H;
+  constexpr int kRows = 2 * L;  // TGSW rows per CMux
+  static_assert(kRows % H == 0, "row groups");
+  constexpr int kRpg = kRows / H;
   constexpr int kScr = scratch_words<H>();
   constexpr int kGateThreads = 64 * H;
   constexpr int kStages = br_stages<H, GT>();
@@ -228,14 +240,18 @@ __device__ __forceinline__ void br_consumer(const BrShared &S, const BrArgs &arg
   uint32_t *D = S.dig + g * 2 * kN;
   uint16_t *abar = S.abar + g * kAbarPitch;
   uint32_t *myscr = S.scratch + (wbase + role) * kScr;
-  const PrimeRT pr = prime_rt(P, args.tc);
+  PrimeRT pr = prime_rt(P, args.tc);
+  if (L == 2) {  // first-stage offsets of 10-bit digits
+    pr.dc = args.tc.dig_c2[P];
+    pr.dd = args.tc.dig_d2[P];
+  }
   const uint2 *tw1f = args.tc.fwd1[P];
   const uint2 *tw1i = args.tc.inv1[P];
   const uint2 *tw2f = args.tg->fwd2[P];
   const uint2 *tw2i = args.tg->inv2[P];
   const uint2 *twist = args.tg->twist[P];
   const int tiles = (args.num_jobs + GT - 1) / GT;
-  const uint32_t rows = cta_rows<GT>(args);
+  const uint32_t rows = cta_rows<GT, L>(args);
   uint32_t it = 0;
 
   for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++it) {
@@ -258,7 +274,7 @@ __device__ __forceinline__ void br_consumer(const BrShared &S, const BrArgs &arg
     named_bar(bar_id, kGateThreads);
 
     for (int i = 0; i < n; ++i) {
-      make_digits<kGateThreads>(D, A, abar[i], tid_g);
+      make_digits<kGateThreads, L>(D, A, abar[i], tid_g);
       named_bar(bar_id, kGateThreads);  // B0: digits ready
       uint32_t acc0[32], acc1[32];
 #pragma unroll
@@ -266,15 +282,21 @@ __device__ __forceinline__ void br_consumer(const BrShared &S, const BrArgs &arg
 #pragma unroll 1
       for (int rr = 0; rr < kRpg; ++rr) {
         const int r = h * kRpg + rr;
-        const int c = r / 3, p = r - 3 * (r / 3);
+        const int c = r / L, p = r - L * (r / L);
         const uint32_t *dc = D + c * kN;
-        const uint32_t sel = 0x4440u | (uint32_t)p;  // byte p of the packed digits, zero-extended
         uint32_t x[32];
+        if constexpr (L == 3) {
+          const uint32_t sel = 0x4440u | (uint32_t)p;  // byte p of the packed digits, zero-extended
 #pragma unroll
-        for (int e = 0; e < 32; ++e) x[e] = __byte_perm(dc[lane + 32 * e], 0u, sel);
+          for (int e = 0; e < 32; ++e) x[e] = __byte_perm(dc[lane + 32 * e], 0u, sel);
+        } else {
+          const uint32_t sh = 16u * (uint32_t)p;  // half p of the packed digits
+#pragma unroll
+          for (int e = 0; e < 32; ++e) x[e] = (dc[lane + 32 * e] >> sh) & 0xFFFFu;
+        }
         ntt_fwd<true>(x, myscr, tw1f, tw2f, pr, lane);
         // MAC with the NTT-domain key row staged in the ring.
-        const uint32_t jc = (it * (uint32_t)n + (uint32_t)i) * 6u + (uint32_t)r;
+        const uint32_t jc = (it * (uint32_t)n + (uint32_t)i) * (uint32_t)kRows + (uint32_t)r;
         const uint32_t slot = jc % kStages;
         mbar_wait(S.full + slot, (jc / kStages) & 1u, S.abort_flag, args.status);
         const uint4 *B0 = reinterpret_cast<const uint4 *>(S.ring + slot * kChunkWords + (cA * 2 + P) * kN);
@@ -298,7 +320,7 @@ __device__ __forceinline__ void br_consumer(const BrShared &S, const BrArgs &arg
           if (atomicAdd(S.cnt + slot, 1u) == 2u * GT - 1u) {
             __threadfence_block();
             S.cnt[slot] = 0u;
-            if (jc + kStages < rows) issue_row<kStages>(S, args, jc + kStages);
+            if (jc + kStages < rows) issue_row<kStages, L>(S, args, jc + kStages);
           }
         }
       }
@@ -383,7 +405,7 @@ __device__ __forceinline__ void br_consumer(const BrShared &S, const BrArgs &arg
   }
 }
 
-template <int H, int GT>
+template <int H, int GT, int L>
 __global__ void __launch_bounds__(2 * H * GT * 32, 1) br_kernel(const __grid_constant__ BrArgs args) {
   extern __shared__ __align__(128) uint8_t smem[];
   BrShared S = br_carve<H, GT>(smem);
@@ -403,11 +425,11 @@ __global__ void __launch_bounds__(2 * H * GT * 32, 1) br_kernel(const __grid_con
   if (threadIdx.x == 0) stamp_start(args.stamps);
   if (args.num_jobs <= 0) return;
   if (threadIdx.x == 0) {  // the first kStages rows; later ones are issued by the warps
-    const uint32_t rows = cta_rows<GT>(args);
-    for (uint32_t jc = 0; jc < (uint32_t)kStages && jc < rows; ++jc) issue_row<kStages>(S, args, jc);
+    const uint32_t rows = cta_rows<GT, L>(args);
+    for (uint32_t jc = 0; jc < (uint32_t)kStages && jc < rows; ++jc) issue_row<kStages, L>(S, args, jc);
   }
   const int g = warp / (2 * H), role = warp % (2 * H);
-  br_consumer<H, GT>(S, args, g, role >> 1, role & 1, lane);
+  br_consumer<H, GT, L>(S, args, g, role >> 1, role & 1, lane);
   __syncthreads();
   if (threadIdx.x == 0 && *S.abort_flag) {  // after a timeout: let copies in flight land (bounded)
     for (int s = 0; s < kStages; ++s) {
@@ -421,33 +443,33 @@ __global__ void __launch_bounds__(2 * H * GT * 32, 1) br_kernel(const __grid_con
   if (lane == 0) stamp_end(args.stamps);
 }
 
-template <int H, int GT>
+template <int H, int GT, int L>
 cudaError_t prepare_shape() {
   static bool done = false;  // calls are serialised by the engine lock
   if (done) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(br_kernel<H, GT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(br_kernel<H, GT, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)br_smem_bytes<H, GT>());
   if (e == cudaSuccess) done = true;
   return e;
 }
 
-template <int H, int GT>
+template <int H, int GT, int L = 3>
 cudaError_t launch_shape(const BrArgs &args, int grid, cudaStream_t st) {
-  cudaError_t e = prepare_shape<H, GT>();
+  cudaError_t e = prepare_shape<H, GT, L>();
   if (e != cudaSuccess) return e;
-  br_kernel<H, GT><<<grid, 2 * H * GT * 32, br_smem_bytes<H, GT>(), st>>>(args);
+  br_kernel<H, GT, L><<<grid, 2 * H * GT * 32, br_smem_bytes<H, GT>(), st>>>(args);
   return cudaGetLastError();
 }
 
 // Resident CTAs per SM of a shape (0 if it cannot launch on this device).
-template <int H, int GT>
+template <int H, int GT, int L = 3>
 int occupancy_shape() {
-  if (prepare_shape<H, GT>() != cudaSuccess) {
+  if (prepare_shape<H, GT, L>() != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
   int blocks = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, br_kernel<H, GT>, 2 * H * GT * 32,
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, br_kernel<H, GT, L>, 2 * H * GT * 32,
                                                     br_smem_bytes<H, GT>()) != cudaSuccess) {
     cudaGetLastError();
     return 0;

@@ -196,12 +196,30 @@ BrShape ShapePolicy::heuristic(int jobs) const {
   if (jobs <= clusters8) return {kCluster8H, 1};
   if (jobs <= clusters4) return {kCluster4H, 1};
   if (jobs <= std::max(clusters2, sms / 2)) return {kClusterH, 1};
+  return wide(jobs);
+}
+
+BrShape ShapePolicy::wide(int jobs) const {
   const int per_sm = (jobs + sms - 1) / sms;
   if (per_sm <= 1) return {6, 1};
   if (per_sm == 2) return {3, 2};
   if (per_sm == 3) return {2, 3};
   if (per_sm <= 4) return {1, 4};
   return {1, 6};
+}
+
+BrShape ShapePolicy::for_gadget(int l, BrShape s, int jobs) const {
+  if (l != 2) return s;
+  const bool cluster = is_cluster_shape(s);
+  if ((!forced.H && jobs <= 2 * std::max(1, clusters8)) || (forced.H && cluster)) return {kCluster8L2H, 1};
+  if (cluster) s = wide(jobs);
+  // rows per warp as close as the 4 rows of l = 2 allow: H 6 -> 4, 3 and 2 -> 2
+  switch (s.H) {
+    case 1: return {kGadget2 + 1, s.GT};
+    case 2: return {kGadget2 + 2, s.GT};
+    case 3: return {kGadget2 + 2, s.GT == 1 ? 1 : 3};
+    default: return {kGadget2 + 4, 1};
+  }
 }
 
 // Autotuned: the shape minimising waves x measured time per wave.
@@ -417,8 +435,8 @@ int plan_build(Engine &E, const arx_netlist *nl, int keyset, int mode, std::uniq
   }
   size_t ks_part_max = 0, ks_gate_max = 0;
   for (Level &L : P->levels) {
-    L.shape = ShapePolicy::for_gadget(
-        P->l, mode == ARX_MODE_GRAPH ? E.policy.pick(L.br_cnt, P->n) : E.policy.heuristic(L.br_cnt));
+    L.shape = E.policy.for_gadget(
+        P->l, mode == ARX_MODE_GRAPH ? E.policy.pick(L.br_cnt, P->n) : E.policy.heuristic(L.br_cnt), L.br_cnt);
     L.grid = E.policy.grid(L.shape, std::max(1, L.br_cnt));
     L.ks_splits = ks_splits(L.ks_cnt, E.sms);
     if (L.ks_splits > 1) {
@@ -584,7 +602,7 @@ int bootstrap_gates(Engine &E, const uint8_t *types, const uint32_t *a, const ui
     args.tg = E.tg;
     args.status = E.status;
     args.tc = E.tc;
-    const BrShape s = ShapePolicy::for_gadget(ks->l, E.policy.pick(args.num_jobs, ks->n));
+    const BrShape s = E.policy.for_gadget(ks->l, E.policy.pick(args.num_jobs, ks->n), args.num_jobs);
     CK(launch_br(args, s, E.policy.grid(s, args.num_jobs), st));
   }
   const bool dev_out = is_device_ptr(out);

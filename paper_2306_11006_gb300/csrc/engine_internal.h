@@ -73,10 +73,14 @@ struct ShapePolicy {
   BrShape forced{0, 0};
   int occupancy(BrShape s);
   BrShape heuristic(int jobs) const;
+  BrShape wide(int jobs) const;  // the throughput shapes of the heuristic
   BrShape pick(int jobs, int n) const;
-  // key sets with gadget l = 2 have one kernel of their own (its four forward
-  // warps already have a scheduler each, so the sixteen-CTA split gains nothing)
-  static BrShape for_gadget(int l, BrShape s) { return l == 2 ? BrShape{kCluster8L2H, 1} : s; }
+  // Key sets with gadget l = 2 (given the shape chosen for l = 3 and the wave's
+  // blind rotations): the eight-CTA kernel of their own while a wave takes at
+  // most two rounds of its clusters (its four forward warps already have a
+  // scheduler each, so the sixteen-CTA split gains nothing), else the throughput
+  // kernel br_kernel<H, GT, 2> on the matching shape.
+  BrShape for_gadget(int l, BrShape s, int jobs) const;
   int grid(BrShape s, int jobs);
 };
 

@@ -14,14 +14,16 @@
 
 namespace arx {
 
-size_t br_smem_h1(int GT);
-size_t br_smem_h2(int GT);
-size_t br_smem_h3(int GT);
-size_t br_smem_h6(int GT);
-int br_occupancy_h1(int GT);
-int br_occupancy_h2(int GT);
-int br_occupancy_h3(int GT);
-int br_occupancy_h6(int GT);
+size_t br_smem_h1(int GT, int L);
+size_t br_smem_h2(int GT, int L);
+size_t br_smem_h3(int GT, int L);
+size_t br_smem_h4(int GT, int L);
+size_t br_smem_h6(int GT, int L);
+int br_occupancy_h1(int GT, int L);
+int br_occupancy_h2(int GT, int L);
+int br_occupancy_h3(int GT, int L);
+int br_occupancy_h4(int GT, int L);
+int br_occupancy_h6(int GT, int L);
 
 namespace {
 
@@ -217,11 +219,13 @@ size_t br_smem(BrShape s) {
   if (s.H == kCluster8H) return s.GT == 1 ? br_cluster8_smem() : 0;
   if (s.H == kCluster8L2H) return s.GT == 1 ? br_cluster8_l2_smem() : 0;
   if (s.H == kCluster16H) return s.GT == 1 ? br_cluster16_smem() : 0;
-  switch (s.H) {
-    case 1: return br_smem_h1(s.GT);
-    case 2: return br_smem_h2(s.GT);
-    case 3: return br_smem_h3(s.GT);
-    case 6: return br_smem_h6(s.GT);
+  const int L = s.H > kGadget2 ? 2 : 3, H = s.H > kGadget2 ? s.H - kGadget2 : s.H;
+  switch (H) {
+    case 1: return br_smem_h1(s.GT, L);
+    case 2: return br_smem_h2(s.GT, L);
+    case 3: return br_smem_h3(s.GT, L);
+    case 4: return br_smem_h4(s.GT, L);
+    case 6: return br_smem_h6(s.GT, L);
     default: return 0;
   }
 }
@@ -234,18 +238,20 @@ int br_occupancy(BrShape s) {
   if (s.H == kCluster8H) return s.GT == 1 ? br_cluster8_occupancy() : 0;
   if (s.H == kCluster8L2H) return s.GT == 1 ? br_cluster8_l2_occupancy() : 0;
   if (s.H == kCluster16H) return s.GT == 1 ? br_cluster16_occupancy() : 0;
-  switch (s.H) {
-    case 1: return br_occupancy_h1(s.GT);
-    case 2: return br_occupancy_h2(s.GT);
-    case 3: return br_occupancy_h3(s.GT);
-    case 6: return br_occupancy_h6(s.GT);
+  const int L = s.H > kGadget2 ? 2 : 3, H = s.H > kGadget2 ? s.H - kGadget2 : s.H;
+  switch (H) {
+    case 1: return br_occupancy_h1(s.GT, L);
+    case 2: return br_occupancy_h2(s.GT, L);
+    case 3: return br_occupancy_h3(s.GT, L);
+    case 4: return br_occupancy_h4(s.GT, L);
+    case 6: return br_occupancy_h6(s.GT, L);
     default: return 0;
   }
 }
 
 int br_threads(BrShape s) {
   if (s.H == kCluster8H || s.H == kCluster8L2H || s.H == kCluster16H) return 9 * 32;
-  return is_cluster_shape(s) ? 13 * 32 : 2 * s.H * s.GT * 32;
+  return is_cluster_shape(s) ? 13 * 32 : 2 * (s.H > kGadget2 ? s.H - kGadget2 : s.H) * s.GT * 32;
 }
 
 cudaError_t launch_br(const BrArgs &args, BrShape s, int grid, cudaStream_t st) {
@@ -255,11 +261,13 @@ cudaError_t launch_br(const BrArgs &args, BrShape s, int grid, cudaStream_t st) 
   if (s.H == kCluster8H) return s.GT == 1 ? launch_br_cluster8(args, grid, st) : cudaErrorInvalidValue;
   if (s.H == kCluster8L2H) return s.GT == 1 ? launch_br_cluster8_l2(args, grid, st) : cudaErrorInvalidValue;
   if (s.H == kCluster16H) return s.GT == 1 ? launch_br_cluster16(args, grid, st) : cudaErrorInvalidValue;
-  switch (s.H) {
-    case 1: return launch_br_h1(args, s.GT, grid, st);
-    case 2: return launch_br_h2(args, s.GT, grid, st);
-    case 3: return launch_br_h3(args, s.GT, grid, st);
-    case 6: return launch_br_h6(args, s.GT, grid, st);
+  const int L = s.H > kGadget2 ? 2 : 3, H = s.H > kGadget2 ? s.H - kGadget2 : s.H;
+  switch (H) {
+    case 1: return launch_br_h1(args, s.GT, L, grid, st);
+    case 2: return launch_br_h2(args, s.GT, L, grid, st);
+    case 3: return launch_br_h3(args, s.GT, L, grid, st);
+    case 4: return launch_br_h4(args, s.GT, L, grid, st);
+    case 6: return launch_br_h6(args, s.GT, L, grid, st);
     default: return cudaErrorInvalidValue;
   }
 }

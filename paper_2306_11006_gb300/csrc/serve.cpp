@@ -250,7 +250,7 @@ int run_tick(Server &S, std::vector<std::shared_ptr<Request>> &act) {
       a.tg = S.tg;
       a.status = S.status;
       a.tc = S.tc;
-      const BrShape s = ShapePolicy::for_gadget(head.l, S.policy.pick(a.num_jobs, head.n));
+      const BrShape s = S.policy.for_gadget(head.l, S.policy.pick(a.num_jobs, head.n), a.num_jobs);
       SCK(launch_br(a, s, S.policy.grid(s, a.num_jobs), S.stream));
       S.launches++;
     }

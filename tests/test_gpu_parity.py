@@ -399,22 +399,64 @@ def test_gadget_l2_netlist_and_shapes(O, keys512_l2, _loaded512_l2, mode):
     assert np.array_equal(arx.client_decrypt(512, k.s, out), nl.plain_eval(bits))
 
 
-def test_gadget_l2_wave_wider_than_the_device_sampled(O, keys512_l2, _loaded512_l2):
-    # more gates than co-resident eight-CTA clusters: the persistent loop takes
-    # several tiles per cluster
+@pytest.mark.parametrize("count", [24, 40])
+def test_gadget_l2_wave_wider_than_the_device_sampled(O, keys512_l2, _loaded512_l2, count):
+    # 24: more gates than co-resident eight-CTA clusters (the persistent loop
+    # takes two tiles per cluster); 40: the throughput kernel br_kernel<H, GT, 2>
     k, ks = keys512_l2, _loaded512_l2
-    types = I.random_gate_types(430, 40)
-    xs, ys = I.random_bits(431, 40), I.random_bits(432, 40)
+    types = I.random_gate_types(430, count)
+    xs, ys = I.random_bits(431, count), I.random_bits(432, count)
     ca, cb = k.encrypt(O, I, xs, 433), k.encrypt(O, I, ys, 434)
     out = np.zeros_like(ca)
     arx.bootstrap_gates_ex(types, ca, cb, ca, out, keyset=ks)
     assert np.array_equal(arx.client_decrypt(512, k.s, out), _truth(types, xs, ys, xs))
-    pick = np.array([0, 13, 26, 39])
+    pick = np.array([0, 13, count - 11, count - 1])
     assert np.array_equal(out[pick], k.ctx.gates(types[pick], ca[pick], cb[pick]))
 
 
+# l = 3 override -> the l = 2 throughput shape it maps to (kGadget2 + H, GT)
+GADGET2_SHAPES = [((1, 1), (101, 1)), ((1, 2), (101, 2)), ((1, 4), (101, 4)), ((1, 6), (101, 6)),
+                  ((2, 1), (102, 1)), ((2, 3), (102, 3)), ((3, 2), (102, 3)), ((6, 1), (104, 1))]
+
+
+def test_gadget_l2_every_throughput_shape_ragged(O, keys512_l2, _loaded512_l2):
+    """37 gates (a ragged tail for every gates-per-CTA tile) under each l = 2
+    throughput shape, every output against the oracle."""
+    k, ks = keys512_l2, _loaded512_l2
+    types = np.array([I.BINARY_OPS[j % 6] if j % 9 else I.MUX for j in range(37)], np.uint8)
+    xs, ys, zs = (I.random_bits(440 + j, len(types)) for j in range(3))
+    ca, cb, cc = (k.encrypt(O, I, v, 443 + j) for j, v in enumerate((xs, ys, zs)))
+    want = k.ctx.gates(types, ca, cb, cc)
+    nl = I.union([I.array_multiplier(6)])
+    try:
+        for (H, GT), mapped in GADGET2_SHAPES:
+            arx.set_launch_shape(H, GT)
+            out = np.zeros_like(ca)
+            arx.bootstrap_gates_ex(types, ca, cb, cc, out, keyset=ks)
+            assert np.array_equal(out, want), (H, GT)
+            with arx.Plan(nl, keyset=ks, mode=arx.MODE_PLAIN) as p:
+                assert all((h, g) == mapped for h, g, j in p.shapes() if j), (H, GT)
+    finally:
+        arx.set_launch_shape(0, 0)
+
+
+def test_gadget_l2_wide_netlist_takes_the_throughput_kernel(O, keys512_l2, _loaded512_l2):
+    k, ks = keys512_l2, _loaded512_l2
+    nl = I.union([I.array_multiplier(8)])  # a 64-gate first wave, then narrow ones
+    bits = I.random_bits(450, nl.num_inputs)
+    ct = k.encrypt(O, I, bits, 451)
+    out = np.zeros((len(nl.outputs), 513), np.uint32)
+    with arx.Plan(nl, keyset=ks, mode=arx.MODE_GRAPH) as p:
+        sh = p.shapes()
+        assert any(H > 100 for H, GT, j in sh if j > 30) and all(H == 40 for H, GT, j in sh if 0 < j <= 30)
+        p.run(ct, out)
+        assert _sampled_gate_parity(O, k, nl, p, per_level=4, levels=6) >= 6
+    assert np.array_equal(arx.client_decrypt(512, k.s, out), nl.plain_eval(bits))
+
+
 def test_gadget_l2_shape_is_not_an_override(gpu630):
-    with pytest.raises(arx.ArxError):
-        arx.set_launch_shape(40, 1)
+    for H, GT in ((40, 1), (101, 6), (104, 1)):
+        with pytest.raises(arx.ArxError):
+            arx.set_launch_shape(H, GT)
     with pytest.raises(arx.ArxError):
         arx._check(arx.lib().arx_load_keys_gadget(None, None, 512, 2, 7, None))
