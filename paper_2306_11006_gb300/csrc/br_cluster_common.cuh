@@ -296,7 +296,7 @@ constexpr uint32_t kDecOffset2 = (1u << 11) + (512u << 22) + (512u << 12);
 // Forward quarter transform with its per-lane twiddles in registers (zc: middle
 // pass, lengths 32, 16, 8; zq: last pass, lengths 4, 2, 1; same entries as the
 // global tables fwdc / fwdq).  In / out as the four-CTA kernel's fwd_quarter:
-// x[e] at p = lane + 32 e (< 5q + 128) -> spectral position 256 Q + 8 b + e,
+// x[e] at p = lane + 32 e (< 5q + 1024: 7- or 10-bit digits) -> spectral position 256 Q + 8 b + e,
 // b = fwd_block8(lane) (< 22q).
 __device__ __forceinline__ void fwd_quarter_r(uint32_t (&x)[8], uint32_t *xbuf, const uint2 *tw1,
                                               const uint2 (&zc)[7], const uint2 (&zq)[7], int Q, const PrimeRT &pr,
