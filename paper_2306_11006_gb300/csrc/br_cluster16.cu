@@ -10,9 +10,10 @@
 //
 // Per CMux: all warps compute the gadget digits of the CTA's three rows and
 // take the first two forward stages of quarter Q in prime P at once
-// (make_stage2); three forward warps (one per row) run the rest of the quarter-Q
-// transform of their row; each adds its key products for output 1-h into CTA (1-h, Q, P)'s receive
-// slot with a bulk reduction (1 KiB) and keeps those for output h.  The inverse
+// (make_stage2); three forward warps (one per row) run the rest of the
+// quarter-Q transform of their row; each adds its key products for output 1-h
+// into CTA (1-h, Q, P)'s receive slot with a bulk reduction (1 KiB) and keeps
+// those for output h.  The inverse
 // warp sums the L local rows and the slot (quarter Q of output h in prime P),
 // runs the inverse quarter transform (all stages but the last two, then the
 // quarter's share of the output twist) and posts it here and at the seven CTAs
@@ -64,7 +65,7 @@ struct Cfg {
 };
 
 __global__ void __launch_bounds__(kThreads, 1) br_cluster16_kernel(const __grid_constant__ BrArgs args) {
-  using C = Cfg;
+  using C = Cfg;  // shared-memory layout
   extern __shared__ __align__(128) uint8_t smem[];
   uint32_t *ring = reinterpret_cast<uint32_t *>(smem);  // [stage][output][N]
   uint32_t *A = reinterpret_cast<uint32_t *>(smem + C::kRingBytes);
