@@ -13,11 +13,11 @@
 // (make_stage2); three forward warps (one per row) run the rest of the
 // quarter-Q transform of their row; each adds its key products for output 1-h
 // into CTA (1-h, Q, P)'s receive slot with a bulk reduction (1 KiB) and keeps
-// those for output h.  The inverse
-// warp sums the L local rows and the slot (quarter Q of output h in prime P),
-// runs the inverse quarter transform (all stages but the last two, then the
-// quarter's share of the output twist) and posts it here and at the seven CTAs
-// (h, Q', P') (1 KiB each).  All eight CTAs of component h then fold the last
+// those for output h.  A pair of inverse warps on two schedulers sums the L
+// local rows and the slot (quarter Q of output h in prime P), runs the inverse
+// quarter transform split between them (inv_quarter_pair: all stages but the
+// last two, then the quarter's share of the output twist) and posts it here and
+// at the seven CTAs (h, Q', P') (1 KiB each).  All eight CTAs of component h then fold the last
 // two stages, run the CRT and update identical copies of ACC_h.  Every
 // cross-CTA dependency is a transaction count on an mbarrier (double-buffered
 // by CMux parity); every wait is bounded.  For the default gadget (l = 3,
@@ -38,7 +38,8 @@ using namespace clu;
 constexpr int kClusterSize = 16;
 constexpr int L = 3;                        // TGSW rows per accumulator component (gadget l = 3)
 constexpr int kCons = 8;                    // three forward warps, the inverse warp, helpers for digits and CRT
-constexpr int kInvWarp = 3;                 // a scheduler of its own
+constexpr int kInvWarp = 3;                 // inverse pair: warps 3 and 4 (schedulers 3 and 0)
+constexpr int kInvWarps = 2;
 constexpr int kThreads = (kCons + 1) * 32;  // + producer warp
 constexpr int kConsThreads = kCons * 32;    // 256
 constexpr int kStages = 6;                  // ring of 8 KiB key rows (one prime, both outputs)
@@ -144,23 +145,21 @@ __global__ void __launch_bounds__(kThreads, 1) br_cluster16_kernel(const __grid_
     const int tid = threadIdx.x;    // 0 .. 255
     const PrimeRT pr = prime_rt(P, args.tc);
     uint32_t *myscr = scratch + warp * kQuarter;
-    const uint2 *tw1f = args.tc.fwd1[P], *tw1i = args.tc.inv1[P];
+    const uint2 *tw1f = args.tc.fwd1[P];
     const uint2 z1 = args.tc.fwd1[P][1], z23 = args.tc.fwd1[P][2 + (Q >> 1)];
     const int fb = fwd_block8(lane);
     const PrimeRT prs[1] = {pr};
     const uint2 z1s[1] = {z1}, z23s[1] = {z23};
     // loop-invariant per-lane twiddles
-    uint2 zc[7], zq[7], zi[7], z2[6], zt[8];
+    uint2 zc[7], zq[7];
 #pragma unroll
     for (int k = 0; k < 7; ++k) {
       zc[k] = __ldg(args.tg->fwdc[P][Q] + k * 32 + lane);
       zq[k] = __ldg(args.tg->fwdq[P][Q] + k * 32 + lane);
-      zi[k] = __ldg(args.tg->invc[P] + k * 32 + lane);
     }
-#pragma unroll
-    for (int k = 0; k < 6; ++k) z2[k] = __ldg(args.tg->inv2[P] + (k + 1) * 32 + lane);
-#pragma unroll
-    for (int e = 0; e < 8; ++e) zt[e] = __ldg(args.tg->fint[P][Q] + lane + 32 * e);
+    const bool inv = warp == kInvWarp || warp == kInvWarp + 1;
+    const int t = lane + 32 * (warp == kInvWarp + 1 ? 1 : 0);  // position index within the inverse pair
+    const InvPairTw zp = load_inv_pair(args, P, Q, t);
     uint32_t it = 0, cm = 0;  // tile counter, CMux counter
     for (int tile = cid; tile < tiles; tile += nclusters, ++it) {
       const BrJob jb = args.jobs[tile];
@@ -215,41 +214,36 @@ __global__ void __launch_bounds__(kThreads, 1) br_cluster16_kernel(const __grid_
           }
           __syncwarp();
           if (lane == 0) mbar_arrive_cta(empty + slot);
-          named_bar_arrive(2, 32 * (L + 1));  // the L rows of output h, quarter Q, in place
-        } else if (warp == kInvWarp) {
-          if (lane == 0) {
+          named_bar_arrive(2, 32 * (L + kInvWarps));  // the L rows of output h, quarter Q, in place
+        } else if (inv) {
+          if (warp == kInvWarp && lane == 0) {
             mbar_expect_tx(done1 + par, C::kPeerBytes);
             mbar_expect_tx(done2 + par, kPartnerBytes);
           }
-          named_bar(2, 32 * (L + 1));
-          // quarter Q of output h in prime P: L local rows and the peer's sum
+          named_bar(2, 32 * (L + kInvWarps));
+          // quarter Q of output h in prime P: L local rows and the peer's sum, at 4 t + e
           mbar_wait(done1 + par, ph, abort_flag, args.status);
-          uint32_t y[8];
-#pragma unroll
-          for (int e = 0; e < 8; ++e) y[e] = 0u;
+          uint32_t y[4] = {0u, 0u, 0u, 0u};
+          const int ci = swp(4 * t) >> 2;
 #pragma unroll
           for (int r4 = 0; r4 <= L; ++r4) {
             uint4 *sl = reinterpret_cast<uint4 *>(r4 < L ? own + r4 * kQuarter : slots + par * kQuarter);
-#pragma unroll
-            for (int c = 0; c < 2; ++c) {
-              const int ci = swp(8 * lane + 4 * c) >> 2;
-              const uint4 q = sl[ci];
-              y[4 * c + 0] += q.x;
-              y[4 * c + 1] += q.y;
-              y[4 * c + 2] += q.z;
-              y[4 * c + 3] += q.w;
-              if (r4 == L) sl[ci] = make_uint4(0u, 0u, 0u, 0u);  // the slot starts its next use at zero
-            }
+            const uint4 q = sl[ci];
+            y[0] += q.x;
+            y[1] += q.y;
+            y[2] += q.z;
+            y[3] += q.w;
+            if (r4 == L) sl[ci] = make_uint4(0u, 0u, 0u, 0u);  // the slot starts its next use at zero
           }
           fence_proxy_async_smem();  // the zeroes precede the peer's next bulk additions
-          inv_quarter_r(y, myscr, tw1i, zi, z2, zt, pr, lane);
+          inv_quarter_pair(y, scratch + kInvWarp * kQuarter, scratch + (kInvWarp + 1) * kQuarter, zp, pr, t, 3);
           // post the quarter here and at the seven CTAs (h, Q', P') (ranks rank ^ 2 j)
           uint32_t *pq = post + ((par * 2 + P) * 4 + Q) * kQuarter;
 #pragma unroll
-          for (int e = 0; e < 8; ++e) pq[lane + 32 * e] = y[e];
+          for (int e = 0; e < 4; ++e) pq[t + 64 * e] = y[e];
           fence_proxy_async_smem();
-          __syncwarp();
-          if (lane < 7) {
+          named_bar(3, 64);  // both halves in place
+          if (warp == kInvWarp && lane < 7) {
             const uint32_t dst = rank ^ (2u * (uint32_t)(lane + 1));
             bulk_s2peer(map_peer(smem_u32(pq), dst), pq, kQuarter * 4u, map_peer(smem_u32(done2 + par), dst));
           }

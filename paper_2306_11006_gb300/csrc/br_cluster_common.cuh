@@ -443,6 +443,90 @@ __device__ __forceinline__ void make_stage2(uint32_t *S, const uint32_t *A, uint
   }
 }
 
+// The inverse quarter transform on a pair of warps (w = 0, 1 of the pair, t =
+// lane + 32 w): the butterflies, twiddles and stage order of inv_quarter_r, in
+// four register passes of two stages on 4 values per lane (half-lengths 1-2,
+// 4-8, 16-32, 64-128), joined by re-layouts through two shared buffers of 256
+// words (XOR-swizzled by isw: every write and read conflict-free).  Stages up to
+// half-length 64 stay inside the warp's half of the quarter (positions
+// [128 w, 128 w + 128)), so the first two re-layouts need only __syncwarp; the
+// last, before half-length 128, goes through the pair's named barrier.  Each
+// butterfly's twiddle depends only on (h, p mod h); the per-lane values come
+// from the same tables (load_inv_pair).
+// In: x[e] at position 4 t + e (< 12 q); out: the twisted result at t + 64 e (< 2q).
+struct InvPairTw {
+  uint2 a[3];     // h = 1 (j = 0), h = 2 (j = 0, 1): inv1[0 .. 2]
+  uint2 b4;       // h = 4, j = t & 3
+  uint2 b8[2];    // h = 8, j = (t & 3) + 4 m
+  uint2 c16;      // h = 16, j = t & 15
+  uint2 c32[2];   // h = 32, j = (t & 15) + 16 m
+  uint2 d64;      // h = 64, j = t
+  uint2 d128[2];  // h = 128, j = t + 64 m
+  uint2 tw[4];    // output twist of quarter Q at t + 64 e
+};
+
+__device__ __forceinline__ int isw(int p) { return p ^ ((p >> 2) & 31); }
+
+__device__ __forceinline__ InvPairTw load_inv_pair(const BrArgs &args, int P, int Q, int t) {
+  InvPairTw z;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) z.a[k] = args.tc.inv1[P][k];
+  z.b4 = args.tc.inv1[P][3 + (t & 3)];
+  const uint2 *invc = args.tg->invc[P], *inv2 = args.tg->inv2[P];
+#pragma unroll
+  for (int m = 0; m < 2; ++m) {
+    z.b8[m] = __ldg(invc + (t & 3) + 4 * m);
+    const int j32 = (t & 15) + 16 * m, j128 = t + 64 * m;
+    z.c32[m] = __ldg(invc + (3 + (j32 >> 3)) * 32 + (j32 & 7));
+    z.d128[m] = __ldg(inv2 + (3 + (j128 >> 5)) * 32 + (j128 & 31));
+  }
+  z.c16 = __ldg(invc + (1 + ((t & 15) >> 3)) * 32 + (t & 7));
+  z.d64 = __ldg(inv2 + (1 + (t >> 5)) * 32 + (t & 31));
+#pragma unroll
+  for (int e = 0; e < 4; ++e) z.tw[e] = __ldg(args.tg->fint[P][Q] + t + 64 * e);
+  return z;
+}
+
+__device__ __forceinline__ void inv_quarter_pair(uint32_t (&x)[4], uint32_t *buf0, uint32_t *buf1,
+                                                 const InvPairTw &z, const PrimeRT &pr, int t, int bar) {
+  // pass A: half-lengths 1, 2 on positions 4 t + e
+  ct_bfly(x[0], x[1], z.a[0], pr);
+  ct_bfly(x[2], x[3], z.a[0], pr);
+  ct_bfly(x[0], x[2], z.a[1], pr);
+  ct_bfly(x[1], x[3], z.a[2], pr);
+#pragma unroll
+  for (int e = 0; e < 4; ++e) buf0[isw(4 * t + e)] = x[e];
+  __syncwarp();
+  const int pb = (t & 3) + 16 * (t >> 2);  // pass B: positions pb + 4 e
+#pragma unroll
+  for (int e = 0; e < 4; ++e) x[e] = buf0[isw(pb + 4 * e)];
+  ct_bfly(x[0], x[1], z.b4, pr);
+  ct_bfly(x[2], x[3], z.b4, pr);
+  ct_bfly(x[0], x[2], z.b8[0], pr);
+  ct_bfly(x[1], x[3], z.b8[1], pr);
+#pragma unroll
+  for (int e = 0; e < 4; ++e) buf1[isw(pb + 4 * e)] = x[e];
+  __syncwarp();
+  const int pcc = (t & 15) + 64 * (t >> 4);  // pass C: positions pcc + 16 e
+#pragma unroll
+  for (int e = 0; e < 4; ++e) x[e] = buf1[isw(pcc + 16 * e)];
+  ct_bfly(x[0], x[1], z.c16, pr);
+  ct_bfly(x[2], x[3], z.c16, pr);
+  ct_bfly(x[0], x[2], z.c32[0], pr);
+  ct_bfly(x[1], x[3], z.c32[1], pr);
+#pragma unroll
+  for (int e = 0; e < 4; ++e) buf0[isw(pcc + 16 * e)] = x[e];
+  named_bar(bar, 64);
+#pragma unroll
+  for (int e = 0; e < 4; ++e) x[e] = buf0[isw(t + 64 * e)];  // pass D: positions t + 64 e
+  ct_bfly(x[0], x[1], z.d64, pr);
+  ct_bfly(x[2], x[3], z.d64, pr);
+  ct_bfly(x[0], x[2], z.d128[0], pr);
+  ct_bfly(x[1], x[3], z.d128[1], pr);
+#pragma unroll
+  for (int e = 0; e < 4; ++e) x[e] = shoup_mul(z.tw[e].x, z.tw[e].y, x[e], pr.q);
+}
+
 // Last two inverse stages and CRT of both primes, then ACC += the Torus32
 // result: post0[Q] holds quarter Q of prime 0 (twisted, natural order), prime 1
 // lies poff1 words above it.
