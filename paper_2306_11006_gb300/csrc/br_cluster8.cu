@@ -54,7 +54,8 @@ struct Cfg {
   static constexpr size_t kOthBytes = 2 * 2 * L * kQuarter * 4;   // [parity][prime][row][quarter Q] for output 1-h
   static constexpr size_t kSlotBytes = 2 * 2 * kQuarter * 4;      // [parity][prime][quarter Q] the peer's row sums
   static constexpr size_t kPostBytes = 2 * 2 * 4 * kQuarter * 4;  // [parity][prime][quarter][k] inverse quarters
-  static constexpr size_t kScrBytes = (size_t)kFwd * kQuarter * 4;
+  static constexpr bool kInvPair = L == 2;  // the inverse on a pair of warps (measured faster only for L = 2)
+  static constexpr size_t kScrBytes = (size_t)(kFwd + (kInvPair ? 2 : 0)) * kQuarter * 4;
   static constexpr size_t kAbarBytes = kAbarPitch * 2;
   static constexpr size_t kBarBytes = (2 * kStages + 4) * 8 + 16;
   static constexpr size_t kSmem = kRingBytes + kAccBytes + kDigBytes + kOwnBytes + kOthBytes + kSlotBytes +
@@ -75,7 +76,7 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(kThreads, 1)
   uint32_t *slots = oth + 4 * L * kQuarter;      // [parity][prime][256], same layout, zero between uses
   uint32_t *post = slots + 4 * kQuarter;         // [parity][prime][quarter][256], natural order
   uint32_t *scratch = post + 16 * kQuarter;      // [forward warp][256]
-  uint16_t *abar = reinterpret_cast<uint16_t *>(scratch + kFwd * kQuarter);
+  uint16_t *abar = reinterpret_cast<uint16_t *>(scratch + C::kScrBytes / 4);
   uint64_t *full = reinterpret_cast<uint64_t *>(abar + kAbarPitch);
   uint64_t *empty = full + kStages;
   uint64_t *done1 = empty + kStages;             // [parity]: the peer's row sums in place
@@ -152,6 +153,9 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(kThreads, 1)
     const uint2 z23s[2] = {args.tc.fwd1[0][2 + (Q >> 1)], args.tc.fwd1[1][2 + (Q >> 1)]};
     uint32_t *myscr = scratch + (fwd ? warp : 0) * kQuarter;
     const uint2 *tw1f = args.tc.fwd1[P], *tw1i = args.tc.inv1[P];
+    // L = 2: the inverse of prime P on the pair of forward warps P (rows rr = 0)
+    // and 2 + P (rr = 1), each holding half of the quarter
+    const int t = lane + (warp >= 2 ? 32 : 0);
     const int fb = fwd_block8(lane);
     // loop-invariant per-lane twiddles
     uint2 zc[7], zq[7], zi[7], z2[6], zt[8];
@@ -165,6 +169,7 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(kThreads, 1)
     for (int k = 0; k < 6; ++k) z2[k] = __ldg(args.tg->inv2[P] + (k + 1) * 32 + lane);
 #pragma unroll
     for (int e = 0; e < 8; ++e) zt[e] = __ldg(args.tg->fint[P][Q] + lane + 32 * e);
+    const InvPairTw zp = load_inv_pair(args, P, Q, t);
     uint32_t it = 0, cm = 0;  // tile counter, CMux counter
     for (int tile = cid; tile < tiles; tile += nclusters, ++it) {
       const BrJob jb = args.jobs[tile];
@@ -224,7 +229,36 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(kThreads, 1)
             mbar_expect_tx(done1 + par, C::kPeerBytes);
             mbar_expect_tx(done2 + par, kPartnerBytes);
           }
-          if (rr == 0) {
+          if constexpr (C::kInvPair) {
+            if (warp < 4) {
+              // quarter Q of output h in prime P: L local rows and the peer's sum, at 4 t + e
+              mbar_wait(done1 + par, ph, abort_flag, args.status);
+              uint32_t y[4] = {0u, 0u, 0u, 0u};
+              const int ci = swp(4 * t) >> 2;
+#pragma unroll
+              for (int r4 = 0; r4 <= L; ++r4) {
+                uint4 *sl = reinterpret_cast<uint4 *>(r4 < L ? own + (P * L + r4) * kQuarter : slots + (par * 2 + P) * kQuarter);
+                const uint4 q = sl[ci];
+                y[0] += q.x;
+                y[1] += q.y;
+                y[2] += q.z;
+                y[3] += q.w;
+                if (r4 == L) sl[ci] = make_uint4(0u, 0u, 0u, 0u);  // the slot starts its next use at zero
+              }
+              fence_proxy_async_smem();  // the zeroes precede the peer's next bulk additions
+              inv_quarter_pair(y, scratch + P * kQuarter, scratch + (kFwd + P) * kQuarter, zp, pr, t, 4 + P);
+              // post the quarter here and at the three CTAs (h, Q')
+              uint32_t *pq = post + ((par * 2 + P) * 4 + Q) * kQuarter;
+#pragma unroll
+              for (int e = 0; e < 4; ++e) pq[t + 64 * e] = y[e];
+              fence_proxy_async_smem();
+              named_bar(4 + P, 64);  // both halves in place
+              if (warp < 2 && lane < 3) {
+                const uint32_t dst = rank ^ (2u * (uint32_t)(lane + 1));  // (h, Q ^ (lane + 1))
+                bulk_s2peer(map_peer(smem_u32(pq), dst), pq, kQuarter * 4u, map_peer(smem_u32(done2 + par), dst));
+              }
+            }
+          } else if (rr == 0) {
             // quarter Q of output h in prime P: L local rows and the peer's sum
             mbar_wait(done1 + par, ph, abort_flag, args.status);
             uint32_t y[8];
