@@ -61,7 +61,7 @@ TRAFFIC_PER_LAUNCH = {
     "br_cluster16_kernel": 62.05e6 + 2.22e6,  # 7 gates
     "br_cluster8_kernel": 62.06e6 + 2.08e6,   # 8 gates
     "br_kernel<1,6>": 66.84e6 + 2.66e6,       # 912 gates
-    "br_cluster8_kernel<L=2>": 33.68e6 + 1.02e6,  # 8 gates, n = 512, l = 2
+    "br_cluster8_kernel<L=2>": 33.68e6 + 6.40e6,  # 8 gates, n = 512, l = 2
     "br_kernel<4,1,L=2>": 34.23e6 + 3.58e6,       # 128 gates, n = 512, l = 2
 }
 
