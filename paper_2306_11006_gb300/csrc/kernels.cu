@@ -157,13 +157,29 @@ __global__ void __launch_bounds__(kKsThreads) ks_kernel(const __grid_constant__ 
   if (!last) return;
   __threadfence();
   if (live) {
-    uint4 sum = make_uint4(0u, 0u, 0u, 0u);
-    for (int q = 0; q < S; ++q) {
-      const uint4 v = __ldcg(part + (size_t)q * kKsVec + t);
-      sum.x += v.x;
-      sum.y += v.y;
-      sum.z += v.z;
-      sum.w += v.w;
+    // eight loads in flight, eight partial sums (u32 additions mod 2^32 in any order)
+    uint4 s8[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) s8[u] = make_uint4(0u, 0u, 0u, 0u);
+    for (int q0 = 0; q0 < S; q0 += 8) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        if (q0 + u < S) {
+          const uint4 v = __ldcg(part + (size_t)(q0 + u) * kKsVec + t);
+          s8[u].x += v.x;
+          s8[u].y += v.y;
+          s8[u].z += v.z;
+          s8[u].w += v.w;
+        }
+      }
+    }
+    uint4 sum = s8[0];
+#pragma unroll
+    for (int u = 1; u < 8; ++u) {
+      sum.x += s8[u].x;
+      sum.y += s8[u].y;
+      sum.z += s8[u].z;
+      sum.w += s8[u].w;
     }
     if (4 * t + 0 <= n) dst[4 * t + 0] = sum.x;
     if (4 * t + 1 <= n) dst[4 * t + 1] = sum.y;
