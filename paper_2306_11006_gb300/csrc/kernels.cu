@@ -119,10 +119,10 @@ __global__ void __launch_bounds__(kKsThreads) ks_kernel(const __grid_constant__ 
   const bool live = t < kKsVec;
   const uint4 *__restrict__ ksk = reinterpret_cast<const uint4 *>(args.ksk);
 #pragma unroll 1
-  for (int i = i0; i < i1; i += 2) {
-    uint4 r[16];
+  for (int i = i0; i < i1; i += 4) {  // 4 positions x 8 digits: 32 key rows in flight (kN / S >= 16)
+    uint4 r[32];
 #pragma unroll
-    for (int u = 0; u < 2; ++u) {
+    for (int u = 0; u < 4; ++u) {
       const uint32_t y = lwe[i + u] + (1u << 15);  // round to 16 bits
 #pragma unroll
       for (int j = 1; j <= 8; ++j) {
@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(kKsThreads) ks_kernel(const __grid_constant__ 
       }
     }
 #pragma unroll
-    for (int q = 0; q < 16; ++q) {
+    for (int q = 0; q < 32; ++q) {
       acc.x -= r[q].x;
       acc.y -= r[q].y;
       acc.z -= r[q].z;
