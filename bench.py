@@ -87,8 +87,12 @@ def replica_seed(base: int, rank: int) -> int:
     return base + rank
 
 
-def workload(name: str, gates: int = 64, blocks: int = 8):
+def workload(name: str, gates: int = 64, blocks: int = 8, copies: int = 1):
     if name == "netlists":
+        if copies > 1:  # independent copies whose ready gates share every launch
+            return I.union([I.ripple_carry_adder(32), I.array_multiplier(8)] * copies,
+                           name=f"{copies}x(adder32+mult8)"), \
+                f"{copies} copies of the 32-bit ripple-carry adder + 8x8 array multiplier, batched per wave"
         return I.union([I.ripple_carry_adder(32), I.array_multiplier(8)], name="adder32+mult8"), \
             "32-bit ripple-carry adder + 8x8 array multiplier (plain netlists, one wave per launch)"
     if name in ("gates", "gates64"):
@@ -343,6 +347,7 @@ def main():
     ap.add_argument("--requests", type=int, default=32, help="serve: requests per run")
     ap.add_argument("--gates", type=int, default=64, help="gate count of the independent-gates workload")
     ap.add_argument("--blocks", type=int, default=8, help="cipher blocks of the simon workload")
+    ap.add_argument("--copies", type=int, default=1, help="netlists: independent copies batched per wave")
     ap.add_argument("--shape", default=None, help="force the blind-rotation launch shape H,GT")
     ap.add_argument("--mode", default="graph", choices=["graph", "plain"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -359,7 +364,7 @@ def main():
             nl, desc = workload("dag")
             return run_reference(args, nl, "serving request mix (oracle on its gate types)")
         return run_serve(args)
-    nl, desc = workload(args.workload, args.gates, args.blocks)
+    nl, desc = workload(args.workload, args.gates, args.blocks, args.copies)
     if args.impl == "reference":
         return run_reference(args, nl, desc)
 
