@@ -211,7 +211,8 @@ BrShape ShapePolicy::wide(int jobs) const {
 BrShape ShapePolicy::for_gadget(int l, BrShape s, int jobs) const {
   if (l != 2) return s;
   const bool cluster = is_cluster_shape(s);
-  if ((!forced.H && jobs <= 2 * std::max(1, clusters8)) || (forced.H && cluster)) return {kCluster8L2H, 1};
+  // (the eight-CTA kernel only where the device co-schedules eight-CTA clusters)
+  if (clusters8 > 0 && ((!forced.H && jobs <= 2 * clusters8) || (forced.H && cluster))) return {kCluster8L2H, 1};
   if (cluster) s = wide(jobs);
   // rows per warp as close as the 4 rows of l = 2 allow: H 6 -> 4, 3 and 2 -> 2
   switch (s.H) {
