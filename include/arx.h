@@ -258,6 +258,19 @@ int arx_keyswitch_noalloc(const uint32_t *lwe_N, uint32_t *ct_out, size_t count,
 const char *arx_last_error(void);
 /* Reads and clears the device watchdog status: ARX_OK or ARX_ETIMEOUT. */
 int arx_device_status(void);
+/* Self-test of the device watchdog (no counterpart in the paper).  One CTA of
+ * four warps waits, through the same bounded wait functions as the kernels, on
+ * one phase of an mbarrier that expects one arrival; post_token != 0 makes that
+ * arrival before the waits, post_token == 0 withholds it, so that every wait
+ * runs out after limit_cycles SM clock cycles (1000 .. 4e9; the kernels use
+ * 4e9, about 2 s), sets the device status word and returns.  Synchronous, on
+ * the library's stream; allocates and frees 16 bytes of device memory.
+ * *waits_given_up (host pointer, may be NULL) receives how many of the four
+ * warps gave up.  Returns ARX_OK (every wait completed), ARX_ETIMEOUT (the
+ * status word recorded the expiry; it is cleared, and the device stays usable),
+ * ARX_EINVAL (limit out of range) or ARX_ECUDA.  An expiry left over from an
+ * earlier call is returned as ARX_ETIMEOUT before anything is launched. */
+int arx_watchdog_selftest(int post_token, long long limit_cycles, int *waits_given_up);
 /* Number of SMs of the device in use (0 before the first call that needs it). */
 int arx_device_sms(void);
 

@@ -71,6 +71,7 @@ SIGNATURES = {
     "arx_serve_stop": (_i, []),
     "arx_last_error": (ctypes.c_char_p, []),
     "arx_device_status": (_i, []),
+    "arx_watchdog_selftest": (_i, [_i, ctypes.c_longlong, _vp]),
     "arx_device_sms": (_i, []),
     "arx_probe_alu": (_i, [_vp, _i]),
     "arx_client_keygen": (_i, [_i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
@@ -317,6 +318,13 @@ def set_launch_shape(H: int = 0, GT: int = 0) -> None:
 
 def device_status() -> int:
     return lib().arx_device_status()
+
+
+def watchdog_selftest(post_token: bool, limit_cycles: int = 20_000_000) -> tuple:
+    """Runs arx_watchdog_selftest; returns (status code, waits given up)."""
+    gave_up = ctypes.c_int(-1)
+    rc = lib().arx_watchdog_selftest(1 if post_token else 0, int(limit_cycles), ctypes.byref(gave_up))
+    return rc, gave_up.value
 
 
 def device_sms() -> int:

@@ -19,7 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libarx.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU = ["br_h1.cu", "br_h2.cu", "br_h3.cu", "br_h4.cu", "br_h6.cu", "br_cluster.cu", "br_cluster4.cu", "br_cluster8.cu", "br_cluster16.cu", "kernels.cu", "noalloc.cu", "probe.cu"]
+CU = ["br_h1.cu", "br_h2.cu", "br_h3.cu", "br_h4.cu", "br_h6.cu", "br_cluster.cu", "br_cluster4.cu", "br_cluster8.cu", "br_cluster16.cu", "kernels.cu", "noalloc.cu", "probe.cu", "watchdog.cu"]
 CPP = ["engine.cpp", "serve.cpp", "twiddles.cpp", "client.cpp"]
 
 

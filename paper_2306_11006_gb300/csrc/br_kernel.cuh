@@ -76,15 +76,16 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
 
 // Bounded wait: a phase that has already completed returns at once (the abort
 // flag is read only on the slow path); returns false (and flags the CTA and the
-// device status) on timeout.
+// device status) once `limit` clock64 cycles have passed (kWaitCycles in the
+// kernel).
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
-                                          unsigned int *status) {
+                                          unsigned int *status, long long limit = kWaitCycles) {
   if (mbar_try_wait(bar, parity)) return true;
   if (*abort_flag) return false;
   long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
     if (*abort_flag) return false;
-    if (clock64() - t0 > kWaitCycles) {
+    if (clock64() - t0 > limit) {
       *abort_flag = 1;
       atomicOr(status, kDevTimeout);
       return false;

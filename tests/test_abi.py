@@ -31,6 +31,13 @@ def test_library_exports_every_declared_symbol():
     assert names == set(arx.SIGNATURES), names ^ set(arx.SIGNATURES)
 
 
+def test_watchdog_selftest_rejects_bad_limits_without_a_device():
+    # checked before the library touches CUDA, so this runs without a GPU
+    for limit in (0, 999, 4_000_000_001):
+        rc, gave_up = arx.watchdog_selftest(False, limit)
+        assert (rc, gave_up) == (-1, -1), limit
+
+
 def test_header_gate_numbering_matches_oracle(O):
     text = open(HEADER).read()
     body = text[text.index("ARX_AND = 0"): text.index("} arx_gate;")]

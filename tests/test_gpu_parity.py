@@ -158,6 +158,22 @@ def test_second_keyset_smaller_dimension(O, keys64, gpu64, gpu630):
     assert np.array_equal(out, keys64.ctx.gates(types, ca, cb, cc))
 
 
+def test_watchdog_expiry_is_reported_and_the_device_stays_usable(O, keys630, gpu630):
+    # the token posted: every bounded wait of both wait functions completes
+    assert arx.watchdog_selftest(True) == (0, 0)
+    # the token withheld: the four waits give up after 2e7 cycles (about 10 ms),
+    # the device status word records the expiry and the call reports it
+    assert arx.watchdog_selftest(False, 20_000_000) == (-5, 4)
+    assert arx.device_status() == 0  # read and cleared by the call
+    assert arx.watchdog_selftest(True) == (0, 0)
+    # the context is intact: the next bootstraps are still bit-exact
+    types = I.random_gate_types(91, 16)
+    xs, ys, zs, ca, cb, cc = _inputs(O, I, keys630, types, 92)
+    out = np.zeros_like(ca)
+    arx.bootstrap_gates(types, ca, cb, out)
+    assert np.array_equal(out, keys630.ctx.gates(types, ca, cb))
+
+
 def test_invalid_arguments_are_rejected(gpu630):
     with pytest.raises(arx.ArxError) as e:
         arx.bootstrap_gates(np.array([11], np.uint8), np.zeros((1, 631), np.uint32),
