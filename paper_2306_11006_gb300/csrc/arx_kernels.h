@@ -45,6 +45,7 @@ struct TwiddleGlobal {
   uint2 fwdq[2][4][7 * 32];   // forward last pass of quarter Q (lengths 4, 2, 1): [prime][Q][(2^s - 1) + block][lane]
   uint2 invc[2][7 * 32];      // inverse quarter, middle pass (half-lengths 8, 16, 32): [prime][(2^s - 1) + j][lane]
   uint2 fint[2][4][256];      // split inverse, twist of quarter Q at k < 256: psi^-(c_Q k), c = (1, 5, 3, 7)
+  uint2 fwdz[2][1024];        // every forward twiddle zeta[k] = psi^bitrev10(k) (pair transforms)
 };
 
 enum : uint32_t {

@@ -10,10 +10,11 @@
 //
 // Per CMux: all warps compute the gadget digits of the CTA's three rows and
 // take the first two forward stages of quarter Q in prime P at once
-// (make_stage2); three forward warps (one per row) run the rest of the
-// quarter-Q transform of their row; each adds its key products for output 1-h
-// into CTA (1-h, Q, P)'s receive slot with a bulk reduction (1 KiB) and keeps
-// those for output h.  A pair of inverse warps on two schedulers sums the L
+// (make_stage2); three pairs of forward warps (one pair per row) run the rest
+// of the quarter-Q transform of their row (fwd_quarter_pair); each warp adds
+// its half of the key products for output 1-h into CTA (1-h, Q, P)'s receive
+// slot with a bulk reduction (512 bytes) and keeps those for output h.  A pair
+// of inverse warps on two schedulers (two of the forward warps) sums the L
 // local rows and the slot (quarter Q of output h in prime P), runs the inverse
 // quarter transform split between them (inv_quarter_pair: all stages but the
 // last two, then the quarter's share of the output twist) and posts it here and
@@ -37,9 +38,9 @@ using namespace clu;
 
 constexpr int kClusterSize = 16;
 constexpr int L = 3;                        // TGSW rows per accumulator component (gadget l = 3)
-constexpr int kCons = 8;                    // three forward warps, the inverse warp, helpers for digits and CRT
+constexpr int kCons = 8;                    // six forward warps (two of them the inverse pair), two helpers
+constexpr int kFwd = 2 * L;                 // forward pair of row r: warps r and r + L
 constexpr int kInvWarp = 3;                 // inverse pair: warps 3 and 4 (schedulers 3 and 0)
-constexpr int kInvWarps = 2;
 constexpr int kThreads = (kCons + 1) * 32;  // + producer warp
 constexpr int kConsThreads = kCons * 32;    // 256
 constexpr int kStages = 6;                  // ring of 8 KiB key rows (one prime, both outputs)
@@ -59,11 +60,101 @@ struct Cfg {
   static constexpr size_t kSlotBytes = (size_t)2 * kQuarter * 4;      // [parity] the peer's row sum
   static constexpr size_t kPostBytes = (size_t)2 * 2 * 4 * kQuarter * 4;  // [parity][prime][quarter][k]
   static constexpr size_t kScrBytes = (size_t)kCons * kQuarter * 4;
+  static constexpr size_t kPairBytes = (size_t)L * kQuarter * 4;      // [row] the pass A -> B exchange
   static constexpr size_t kAbarBytes = kAbarPitch * 2;
   static constexpr size_t kBarBytes = (2 * kStages + 4) * 8 + 16;
   static constexpr size_t kSmem = kRingBytes + kAccBytes + kDigBytes + kOwnBytes + kOthBytes + kSlotBytes +
-                                  kPostBytes + kScrBytes + kAbarBytes + kBarBytes;
+                                  kPostBytes + kScrBytes + kPairBytes + kAbarBytes + kBarBytes;
 };
+
+// Conflict-free word offsets of the forward pair's three re-layouts (checked
+// for every access pattern below: 32 distinct banks per warp access).
+__device__ __forceinline__ int s_ab(int p) { return p ^ (((p >> 6) & 1) << 4); }
+__device__ __forceinline__ int s_bc(int p) { return p ^ (((p >> 5) & 1) << 2) ^ (((p >> 6) & 1) * 24); }
+__device__ __forceinline__ int s_cd(int p) { return p ^ (((p >> 5) & 1) * 5) ^ (((p >> 6) & 1) * 10); }
+// 16-byte slot of positions 4 j .. 4 j + 3 in the product buffers (own, oth and
+// the receive slot): conflict-free for the forward pair's stores (j = jl below)
+// and the inverse pair's loads (j = t), and each warp's half (j < 32, j >= 32)
+// stays contiguous for its bulk reduction.
+__device__ __forceinline__ int s_j(int j) { return j ^ (((j >> 3) & 3) << 1); }
+
+// Per-thread twiddles of the forward quarter transform on a pair of warps.  The
+// butterfly of length len on global spectral position g (bit len of g clear)
+// takes zeta[512 / len + g / (2 len)], g = 256 Q + p; see fwd_quarter_pair for
+// the positions each thread holds.
+struct FwdPairTw {
+  uint2 a128, a64[2];  // lengths 128, 64 (the same on every thread)
+  uint2 b32, b16[2];   // 32, 16
+  uint2 c8, c4[2];     // 8, 4
+  uint2 d2, d1[2];     // 2, 1
+};
+
+__device__ __forceinline__ FwdPairTw load_fwd_pair(const BrArgs &args, int P, int Q, int w, int lane) {
+  const uint2 *z = args.tg->fwdz[P];
+  const int l4 = lane >> 4, l2 = lane >> 2, j = 32 * w + 8 * (lane & 3) + l2;
+  FwdPairTw f;
+  f.a128 = __ldg(z + 4 + Q);
+  f.b32 = __ldg(z + 16 + 4 * Q + 2 * w + l4);
+  f.c8 = __ldg(z + 64 + 16 * Q + 8 * w + l2);
+  f.d2 = __ldg(z + 256 + 64 * Q + j);
+#pragma unroll
+  for (int m = 0; m < 2; ++m) {
+    f.a64[m] = __ldg(z + 8 + 2 * Q + m);
+    f.b16[m] = __ldg(z + 32 + 8 * Q + 4 * w + 2 * l4 + m);
+    f.c4[m] = __ldg(z + 128 + 32 * Q + 16 * w + 2 * l2 + m);
+    f.d1[m] = __ldg(z + 512 + 128 * Q + 2 * j + m);
+  }
+  return f;
+}
+
+// Two stages on four values: lengths 2 d (pairs x0-x2, x1-x3, twiddle zo) and
+// d (pairs x0-x1 with zi[0], x2-x3 with zi[1]).
+__device__ __forceinline__ void fwd_radix4(uint32_t (&x)[4], uint2 zo, const uint2 (&zi)[2], const PrimeRT &pr) {
+  ct_bfly(x[0], x[2], zo, pr);
+  ct_bfly(x[1], x[3], zo, pr);
+  ct_bfly(x[0], x[1], zi[0], pr);
+  ct_bfly(x[2], x[3], zi[1], pr);
+}
+
+// The last eight forward stages (lengths 128 .. 1) of spectral quarter Q on a
+// pair of warps (w = 0, 1 of the pair, t = lane + 32 w): the butterflies and
+// twiddles of fwd_quarter_r in four register passes of two stages on 4 values
+// per lane, joined by three re-layouts.  Pass A (lengths 128, 64) reads
+// positions t + 64 e straight from the stage-2 row Dr; from pass B on, warp w
+// holds positions [128 w, 128 w + 128), so only the A -> B re-layout (through
+// the pair buffer pbuf, 256 words) needs the pair's named barrier; B -> C and
+// C -> D go through the warp's own 256 words wbuf.  Out: x[e] = spectral
+// position 256 Q + 4 j + e, j = 32 w + 8 (lane mod 4) + lane / 4 (< 22 q, as
+// fwd_quarter_r).
+__device__ __forceinline__ void fwd_quarter_pair(uint32_t (&x)[4], const uint32_t *Dr, uint32_t *pbuf,
+                                                 uint32_t *wbuf, const FwdPairTw &z, const PrimeRT &pr, int w,
+                                                 int lane, int bar) {
+  const int t = lane + 32 * w;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) x[e] = Dr[t + 64 * e];
+  fwd_radix4(x, z.a128, z.a64, pr);
+#pragma unroll
+  for (int e = 0; e < 4; ++e) pbuf[s_ab(t + 64 * e)] = x[e];
+  named_bar(bar, 64);
+  const int pb = (lane & 15) + 64 * (lane >> 4);  // pass B: local positions pb + 16 e
+#pragma unroll
+  for (int e = 0; e < 4; ++e) x[e] = pbuf[s_ab(128 * w + pb + 16 * e)];
+  fwd_radix4(x, z.b32, z.b16, pr);
+#pragma unroll
+  for (int e = 0; e < 4; ++e) wbuf[s_bc(pb + 16 * e)] = x[e];
+  __syncwarp();
+  const int pc = (lane & 3) + 16 * (lane >> 2);  // pass C: local positions pc + 4 e
+#pragma unroll
+  for (int e = 0; e < 4; ++e) x[e] = wbuf[s_bc(pc + 4 * e)];
+  fwd_radix4(x, z.c8, z.c4, pr);
+#pragma unroll
+  for (int e = 0; e < 4; ++e) wbuf[128 + s_cd(pc + 4 * e)] = x[e];
+  __syncwarp();
+  const int jl = 8 * (lane & 3) + (lane >> 2);  // pass D: local positions 4 jl + e
+#pragma unroll
+  for (int e = 0; e < 4; ++e) x[e] = wbuf[128 + s_cd(4 * jl + e)];
+  fwd_radix4(x, z.d2, z.d1, pr);
+}
 
 __global__ void __launch_bounds__(kThreads, 1) br_cluster16_kernel(const __grid_constant__ BrArgs args) {
   using C = Cfg;  // shared-memory layout
@@ -76,7 +167,8 @@ __global__ void __launch_bounds__(kThreads, 1) br_cluster16_kernel(const __grid_
   uint32_t *slots = oth + 2 * L * kQuarter;      // [parity][256], same layout, zero between uses
   uint32_t *post = slots + 2 * kQuarter;         // [parity][prime][quarter][256], natural order
   uint32_t *scratch = post + 16 * kQuarter;      // [warp][256]
-  uint16_t *abar = reinterpret_cast<uint16_t *>(scratch + kCons * kQuarter);
+  uint32_t *pairbuf = scratch + kCons * kQuarter;  // [row][256]
+  uint16_t *abar = reinterpret_cast<uint16_t *>(pairbuf + L * kQuarter);
   uint64_t *full = reinterpret_cast<uint64_t *>(abar + kAbarPitch);
   uint64_t *empty = full + kStages;
   uint64_t *done1 = empty + kStages;             // [parity]: the peer's row sum in place
@@ -92,7 +184,7 @@ __global__ void __launch_bounds__(kThreads, 1) br_cluster16_kernel(const __grid_
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(full + s, 1);
-      mbar_init(empty + s, 1);  // the forward warp of the row
+      mbar_init(empty + s, 2);  // the forward pair of the row
     }
     for (int p = 0; p < 2; ++p) {
       mbar_init(done1 + p, 1);  // one local arrival (with the expected bytes) per CMux
@@ -140,23 +232,17 @@ __global__ void __launch_bounds__(kThreads, 1) br_cluster16_kernel(const __grid_
       }
     }
   } else if (tiles > 0) {
-    const bool fwd = warp < L;
-    const int rr = fwd ? warp : 0;  // forward warps: row L h + rr
-    const int tid = threadIdx.x;    // 0 .. 255
+    const bool fwd = warp < kFwd;
+    const int rr = fwd ? warp % L : 0;  // forward pairs: row L h + rr on warps rr, rr + L
+    const int fw = fwd ? warp / L : 0;  // the warp's half of the pair
+    const int tid = threadIdx.x;        // 0 .. 255
     const PrimeRT pr = prime_rt(P, args.tc);
-    uint32_t *myscr = scratch + warp * kQuarter;
-    const uint2 *tw1f = args.tc.fwd1[P];
     const uint2 z1 = args.tc.fwd1[P][1], z23 = args.tc.fwd1[P][2 + (Q >> 1)];
-    const int fb = fwd_block8(lane);
+    const int jl = 8 * (lane & 3) + (lane >> 2);  // the forward pair's output block (see fwd_quarter_pair)
+    const int jf = 32 * fw + jl;
     const PrimeRT prs[1] = {pr};
     const uint2 z1s[1] = {z1}, z23s[1] = {z23};
-    // loop-invariant per-lane twiddles
-    uint2 zc[7], zq[7];
-#pragma unroll
-    for (int k = 0; k < 7; ++k) {
-      zc[k] = __ldg(args.tg->fwdc[P][Q] + k * 32 + lane);
-      zq[k] = __ldg(args.tg->fwdq[P][Q] + k * 32 + lane);
-    }
+    const FwdPairTw zf = load_fwd_pair(args, P, Q, fw, lane);  // loop-invariant per-lane twiddles
     const bool inv = warp == kInvWarp || warp == kInvWarp + 1;
     const int t = lane + 32 * (warp == kInvWarp + 1 ? 1 : 0);  // position index within the inverse pair
     const InvPairTw zp = load_inv_pair(args, P, Q, t);
@@ -179,52 +265,46 @@ __global__ void __launch_bounds__(kThreads, 1) br_cluster16_kernel(const __grid_
         make_stage2<L, 1>(D, A, abar[i], z1s, z23s, Q, prs, tid, kConsThreads);
         named_bar(1, kConsThreads);
         if (fwd) {
-          uint32_t x[8];
-#pragma unroll
-          for (int e = 0; e < 8; ++e) x[e] = D[rr * 256 + lane + 32 * e];
-          fwd_quarter_r(x, myscr, tw1f, zc, zq, Q, pr, lane);
+          uint32_t x[4];
+          fwd_quarter_pair(x, D + rr * 256, pairbuf + rr * kQuarter, scratch + warp * kQuarter, zf, pr, fw, lane,
+                           4 + rr);
           const uint32_t jc = (it * (uint32_t)n + (uint32_t)i) * (uint32_t)L + (uint32_t)rr;
           const uint32_t slot = jc % kStages;
           mbar_wait(full + slot, (jc / kStages) & 1u, abort_flag, args.status);
-          // key row layout: position 32 L + E at word ((E >> 2) * 32 + L) * 4 + (E & 3)
+          // key row layout: position 32 L + E at word ((E >> 2) * 32 + L) * 4 + (E & 3), so
+          // positions 256 Q + 4 j .. + 3 are 16-byte word (j mod 8) * 32 + 8 Q + j / 8
           const uint4 *Bown = reinterpret_cast<const uint4 *>(ring + slot * kRowWords + h * kN);
           const uint4 *Both = reinterpret_cast<const uint4 *>(ring + slot * kRowWords + (1 - h) * kN);
+          const int kj = (jf & 7) * 32 + 8 * Q + (jf >> 3);
           uint32_t *oq = oth + (par * L + rr) * kQuarter;
-          uint4 *oth4 = reinterpret_cast<uint4 *>(oq);
-          uint4 *own4 = reinterpret_cast<uint4 *>(own + rr * kQuarter);
           // products for the peer's output first: added into its slot while the rest runs
-#pragma unroll
-          for (int c = 0; c < 2; ++c) {
-            const uint4 b1 = Both[(2 * (fb & 3) + c) * 32 + 8 * Q + (fb >> 2)];
-            oth4[swp(8 * fb + 4 * c) >> 2] =
-                make_uint4(mont_mul(x[4 * c + 0], b1.x, pr), mont_mul(x[4 * c + 1], b1.y, pr),
-                           mont_mul(x[4 * c + 2], b1.z, pr), mont_mul(x[4 * c + 3], b1.w, pr));
-          }
+          const uint4 b1 = Both[kj];
+          reinterpret_cast<uint4 *>(oq)[s_j(jf)] =
+              make_uint4(mont_mul(x[0], b1.x, pr), mont_mul(x[1], b1.y, pr), mont_mul(x[2], b1.z, pr),
+                         mont_mul(x[3], b1.w, pr));
           fence_proxy_async_smem();
           __syncwarp();
-          if (lane == 0)
-            bulk_add_s2peer(map_peer(smem_u32(slots + par * kQuarter), peer), oq, kQuarter * 4u,
-                            map_peer(smem_u32(done1 + par), peer));
-#pragma unroll
-          for (int c = 0; c < 2; ++c) {
-            const uint4 b0 = Bown[(2 * (fb & 3) + c) * 32 + 8 * Q + (fb >> 2)];
-            own4[swp(8 * fb + 4 * c) >> 2] =
-                make_uint4(mont_mul(x[4 * c + 0], b0.x, pr), mont_mul(x[4 * c + 1], b0.y, pr),
-                           mont_mul(x[4 * c + 2], b0.z, pr), mont_mul(x[4 * c + 3], b0.w, pr));
-          }
+          if (lane == 0)  // this warp's half: positions 128 fw .. 128 fw + 127, 512 bytes
+            bulk_add_s2peer(map_peer(smem_u32(slots + par * kQuarter + 128 * fw), peer), oq + 128 * fw,
+                            kQuarter * 2u, map_peer(smem_u32(done1 + par), peer));
+          const uint4 b0 = Bown[kj];
+          reinterpret_cast<uint4 *>(own + rr * kQuarter)[s_j(jf)] =
+              make_uint4(mont_mul(x[0], b0.x, pr), mont_mul(x[1], b0.y, pr), mont_mul(x[2], b0.z, pr),
+                         mont_mul(x[3], b0.w, pr));
           __syncwarp();
           if (lane == 0) mbar_arrive_cta(empty + slot);
-          named_bar_arrive(2, 32 * (L + kInvWarps));  // the L rows of output h, quarter Q, in place
-        } else if (inv) {
+          if (!inv) named_bar_arrive(2, 32 * kFwd);  // the L rows of output h, quarter Q, in place
+        }
+        if (inv) {
           if (warp == kInvWarp && lane == 0) {
             mbar_expect_tx(done1 + par, C::kPeerBytes);
             mbar_expect_tx(done2 + par, kPartnerBytes);
           }
-          named_bar(2, 32 * (L + kInvWarps));
+          named_bar(2, 32 * kFwd);
           // quarter Q of output h in prime P: L local rows and the peer's sum, at 4 t + e
           mbar_wait(done1 + par, ph, abort_flag, args.status);
           uint32_t y[4] = {0u, 0u, 0u, 0u};
-          const int ci = swp(4 * t) >> 2;
+          const int ci = s_j(t);
 #pragma unroll
           for (int r4 = 0; r4 <= L; ++r4) {
             uint4 *sl = reinterpret_cast<uint4 *>(r4 < L ? own + r4 * kQuarter : slots + par * kQuarter);

@@ -72,6 +72,7 @@ void fill(int P, uint64_t q, TwiddleConst *tc, TwiddleGlobal *tg) {
   for (uint32_t k = 1; k < 1024; ++k) zeta[k] = pw(psi, bitrev10(k), q);
   zeta[0] = 1;
   for (int zi = 0; zi < 32; ++zi) tc->fwd1[P][zi] = entry(zeta[zi], q);
+  for (int k = 0; k < 1024; ++k) tg->fwdz[P][k] = entry(zeta[k], q);
   tc->dig_c[P] = (uint32_t)((2 * q - 64 - 64 * zeta[1] % q) % q);
   tc->dig_d[P] = (uint32_t)((64 * zeta[1] % q + q - 64) % q);
   tc->dig_c2[P] = (uint32_t)((2 * q - 512 - 512 * zeta[1] % q) % q);
