@@ -106,7 +106,6 @@ void make_twiddles(TwiddleConst *tc, TwiddleGlobal *tg);
 cudaError_t launch_bsk_to_ntt(const uint32_t *bsk_coef, int n, int rows, uint32_t *bsk_ntt, const TwiddleConst &tc,
                               const TwiddleGlobal *tg, cudaStream_t st);
 size_t br_smem(BrShape s);
-int br_threads(BrShape s);
 bool br_shape_supported(BrShape s);
 int br_occupancy(BrShape s);  // resident CTAs per SM (0: cannot launch)
 cudaError_t launch_br(const BrArgs &args, BrShape s, int grid, cudaStream_t st);

@@ -528,6 +528,96 @@ __device__ __forceinline__ void inv_quarter_pair(uint32_t (&x)[4], uint32_t *buf
   for (int e = 0; e < 4; ++e) x[e] = shoup_mul(z.tw[e].x, z.tw[e].y, x[e], pr.q);
 }
 
+// Conflict-free word offsets of the forward pair's three re-layouts (checked
+// for every access pattern below: 32 distinct banks per warp access).
+__device__ __forceinline__ int s_ab(int p) { return p ^ (((p >> 6) & 1) << 4); }
+__device__ __forceinline__ int s_bc(int p) { return p ^ (((p >> 5) & 1) << 2) ^ (((p >> 6) & 1) * 24); }
+__device__ __forceinline__ int s_cd(int p) { return p ^ (((p >> 5) & 1) * 5) ^ (((p >> 6) & 1) * 10); }
+// 16-byte slot of positions 4 j .. 4 j + 3 in the product buffers (own, oth and
+// the receive slot): conflict-free for the forward pair's stores (j = 32 w +
+// 8 (lane mod 4) + lane / 4), the inverse pair's loads (j = t) and a single
+// inverse warp's loads (j = 2 lane + c), and each warp's half (j < 32, j >= 32)
+// stays contiguous for its bulk reduction.
+__device__ __forceinline__ int s_j(int j) { return j ^ (((j >> 3) & 1) * 3) ^ (((j >> 4) & 1) * 4); }
+
+// Per-thread twiddles of the forward quarter transform on a pair of warps.  The
+// butterfly of length len on global spectral position g (bit len of g clear)
+// takes zeta[512 / len + g / (2 len)], g = 256 Q + p; see fwd_quarter_pair for
+// the positions each thread holds.
+struct FwdPairTw {
+  uint2 a128, a64[2];  // lengths 128, 64 (the same on every thread)
+  uint2 b32, b16[2];   // 32, 16
+  uint2 c8, c4[2];     // 8, 4
+  uint2 d2, d1[2];     // 2, 1
+};
+
+__device__ __forceinline__ FwdPairTw load_fwd_pair(const BrArgs &args, int P, int Q, int w, int lane) {
+  const uint2 *z = args.tg->fwdz[P];
+  const int l4 = lane >> 4, l2 = lane >> 2, j = 32 * w + 8 * (lane & 3) + l2;
+  FwdPairTw f;
+  f.a128 = __ldg(z + 4 + Q);
+  f.b32 = __ldg(z + 16 + 4 * Q + 2 * w + l4);
+  f.c8 = __ldg(z + 64 + 16 * Q + 8 * w + l2);
+  f.d2 = __ldg(z + 256 + 64 * Q + j);
+#pragma unroll
+  for (int m = 0; m < 2; ++m) {
+    f.a64[m] = __ldg(z + 8 + 2 * Q + m);
+    f.b16[m] = __ldg(z + 32 + 8 * Q + 4 * w + 2 * l4 + m);
+    f.c4[m] = __ldg(z + 128 + 32 * Q + 16 * w + 2 * l2 + m);
+    f.d1[m] = __ldg(z + 512 + 128 * Q + 2 * j + m);
+  }
+  return f;
+}
+
+// Two stages on four values: lengths 2 d (pairs x0-x2, x1-x3, twiddle zo) and
+// d (pairs x0-x1 with zi[0], x2-x3 with zi[1]).
+__device__ __forceinline__ void fwd_radix4(uint32_t (&x)[4], uint2 zo, const uint2 (&zi)[2], const PrimeRT &pr) {
+  ct_bfly(x[0], x[2], zo, pr);
+  ct_bfly(x[1], x[3], zo, pr);
+  ct_bfly(x[0], x[1], zi[0], pr);
+  ct_bfly(x[2], x[3], zi[1], pr);
+}
+
+// The last eight forward stages (lengths 128 .. 1) of spectral quarter Q on a
+// pair of warps (w = 0, 1 of the pair, t = lane + 32 w): the butterflies and
+// twiddles of fwd_quarter_r in four register passes of two stages on 4 values
+// per lane, joined by three re-layouts.  Pass A (lengths 128, 64) reads
+// positions t + 64 e straight from the stage-2 row Dr; from pass B on, warp w
+// holds positions [128 w, 128 w + 128), so only the A -> B re-layout (through
+// the pair buffer pbuf, 256 words) needs the pair's named barrier; B -> C and
+// C -> D go through the warp's own 256 words wbuf.  Out: x[e] = spectral
+// position 256 Q + 4 j + e, j = 32 w + 8 (lane mod 4) + lane / 4 (< 22 q, as
+// fwd_quarter_r).
+__device__ __forceinline__ void fwd_quarter_pair(uint32_t (&x)[4], const uint32_t *Dr, uint32_t *pbuf,
+                                                 uint32_t *wbuf, const FwdPairTw &z, const PrimeRT &pr, int w,
+                                                 int lane, int bar) {
+  const int t = lane + 32 * w;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) x[e] = Dr[t + 64 * e];
+  fwd_radix4(x, z.a128, z.a64, pr);
+#pragma unroll
+  for (int e = 0; e < 4; ++e) pbuf[s_ab(t + 64 * e)] = x[e];
+  named_bar(bar, 64);
+  const int pb = (lane & 15) + 64 * (lane >> 4);  // pass B: local positions pb + 16 e
+#pragma unroll
+  for (int e = 0; e < 4; ++e) x[e] = pbuf[s_ab(128 * w + pb + 16 * e)];
+  fwd_radix4(x, z.b32, z.b16, pr);
+#pragma unroll
+  for (int e = 0; e < 4; ++e) wbuf[s_bc(pb + 16 * e)] = x[e];
+  __syncwarp();
+  const int pc = (lane & 3) + 16 * (lane >> 2);  // pass C: local positions pc + 4 e
+#pragma unroll
+  for (int e = 0; e < 4; ++e) x[e] = wbuf[s_bc(pc + 4 * e)];
+  fwd_radix4(x, z.c8, z.c4, pr);
+#pragma unroll
+  for (int e = 0; e < 4; ++e) wbuf[128 + s_cd(pc + 4 * e)] = x[e];
+  __syncwarp();
+  const int jl = 8 * (lane & 3) + (lane >> 2);  // pass D: local positions 4 jl + e
+#pragma unroll
+  for (int e = 0; e < 4; ++e) x[e] = wbuf[128 + s_cd(4 * jl + e)];
+  fwd_radix4(x, z.d2, z.d1, pr);
+}
+
 // Last two inverse stages and CRT of both primes, then ACC += the Torus32
 // result: post0[Q] holds quarter Q of prime 0 (twisted, natural order), prime 1
 // lies poff1 words above it.

@@ -265,11 +265,6 @@ int br_occupancy(BrShape s) {
   }
 }
 
-int br_threads(BrShape s) {
-  if (s.H == kCluster8H || s.H == kCluster8L2H || s.H == kCluster16H) return 9 * 32;
-  return is_cluster_shape(s) ? 13 * 32 : 2 * (s.H > kGadget2 ? s.H - kGadget2 : s.H) * s.GT * 32;
-}
-
 cudaError_t launch_br(const BrArgs &args, BrShape s, int grid, cudaStream_t st) {
   if (args.num_jobs <= 0) return cudaSuccess;
   if (s.H == kClusterH) return s.GT == 1 ? launch_br_cluster(args, grid, st) : cudaErrorInvalidValue;
