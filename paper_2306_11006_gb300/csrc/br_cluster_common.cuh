@@ -535,10 +535,13 @@ __device__ __forceinline__ int s_bc(int p) { return p ^ (((p >> 5) & 1) << 2) ^ 
 __device__ __forceinline__ int s_cd(int p) { return p ^ (((p >> 5) & 1) * 5) ^ (((p >> 6) & 1) * 10); }
 // 16-byte slot of positions 4 j .. 4 j + 3 in the product buffers (own, oth and
 // the receive slot): conflict-free for the forward pair's stores (j = 32 w +
-// 8 (lane mod 4) + lane / 4), the inverse pair's loads (j = t) and a single
-// inverse warp's loads (j = 2 lane + c), and each warp's half (j < 32, j >= 32)
-// stays contiguous for its bulk reduction.
-__device__ __forceinline__ int s_j(int j) { return j ^ (((j >> 3) & 1) * 3) ^ (((j >> 4) & 1) * 4); }
+// 8 (lane mod 4) + lane / 4), a one-warp forward transform's stores (j =
+// 2 fwd_block8(lane) + c), the inverse pair's loads (j = t) and a one-warp
+// inverse's loads (j = 2 lane + c); each warp's half of a pair (j < 32,
+// j >= 32) stays contiguous for its bulk reduction.
+__device__ __forceinline__ int s_j(int j) {
+  return j ^ (((j >> 3) & 1) * 3) ^ (((j >> 4) & 1) * 4) ^ ((j >> 5) & 1);
+}
 
 // Per-thread twiddles of the forward quarter transform on a pair of warps.  The
 // butterfly of length len on global spectral position g (bit len of g clear)
