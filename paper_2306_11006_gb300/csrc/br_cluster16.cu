@@ -5,8 +5,8 @@
 // the remedy for thin waves (Sec. 8).  Here CTA (h, Q, P) of the cluster (rank
 // 4 Q + 2 P + h) owns accumulator component ACC_h, the TGSW rows whose digits
 // come from it (rows L h .. L h + L - 1), spectral quarter Q and one CRT prime P:
-// the eight-CTA kernel's work split once more, by prime, so that each of a
-// CTA's forward warps has a scheduler of its own.
+// the eight-CTA kernel's work split once more, by prime, so that a CTA's
+// forward and inverse transforms can each run on a pair of warps.
 //
 // Per CMux: all warps compute the gadget digits of the CTA's three rows and
 // take the first two forward stages of quarter Q in prime P at once
@@ -18,8 +18,9 @@
 // local rows and the slot (quarter Q of output h in prime P), runs the inverse
 // quarter transform split between them (inv_quarter_pair: all stages but the
 // last two, then the quarter's share of the output twist) and posts it here and
-// at the seven CTAs (h, Q', P') (1 KiB each).  All eight CTAs of component h then fold the last
-// two stages, run the CRT and update identical copies of ACC_h.  Every
+// at the seven CTAs (h, Q', P') (1 KiB each).  All eight CTAs of component h
+// then fold the last two stages, run the CRT and update identical copies of
+// ACC_h.  Every
 // cross-CTA dependency is a transaction count on an mbarrier (double-buffered
 // by CMux parity); every wait is bounded.  For the default gadget (l = 3,
 // Bg = 2^7) only: with l = 2 the eight-CTA kernel's four forward warps already
