@@ -445,7 +445,7 @@ def main():
     for H, GT, jobs in plan.shapes():
         if jobs:
             k = {12: "br_cluster_kernel", 24: "br_cluster4_kernel", 48: "br_cluster8_kernel",
-                 40: "br_cluster8_kernel<L=2>", 96: "br_cluster16_kernel"}.get(
+                 40: "br_cluster8_kernel<L=2>", 80: "br_cluster16_kernel<L=2>", 96: "br_cluster16_kernel"}.get(
                      H, f"br_kernel<{H - 100},{GT},L=2>" if H > 100 else f"br_kernel<{H},{GT}>")
             waves_of[k] = waves_of.get(k, 0) + 1
     br_kernels = sorted(waves_of, key=lambda k: -waves_of[k])  # dominant (most waves) first

@@ -166,8 +166,8 @@ int arx_plan_info(int plan, uint32_t *waves, uint64_t *bootstraps, uint64_t *gat
  * chose when the plan was created): for wave w < min(cap, waves), H[w] and
  * GT[w] as in arx_set_launch_shape ((96, 1) / (48, 1) / (24, 1) / (12, 1): the
  * sixteen- / eight- / four- / two-CTA cluster kernels; for key sets with
- * gadget l = 2, (40, 1) their eight-CTA kernel and (100 + H, GT) the
- * throughput kernel with 2H warps per gate) and
+ * gadget l = 2, (80, 1) / (40, 1) their sixteen- / eight-CTA kernels and
+ * (100 + H, GT) the throughput kernel with 2H warps per gate) and
  * jobs[w] = its blind rotations (0 for a wave of linear gates only, which
  * launches no blind rotation).  Host arrays; any may be NULL.  Returns the
  * number of waves.  No counterpart in the paper: introspection only. */
@@ -191,10 +191,12 @@ int arx_plan_profile(int plan, const uint32_t *ct_in, float *br_ms, float *ks_ms
  * cluster size).  (0, 0) restores the automatic choice.
  * Shapes: (96,1) (48,1) (24,1) (12,1) (6,1) (3,1) (3,2) (2,1) (2,3) (1,1) (1,2)
  * (1,4) (1,6).  Plans keep the shapes chosen when they were created.  Key sets
- * with gadget l = 2 run kernels of their own: the eight-CTA one, (40, 1), for
+ * with gadget l = 2 run kernels of their own: the sixteen-CTA one, (80, 1),
+ * for waves that fit its co-resident clusters, the eight-CTA one, (40, 1), for
  * waves of up to two rounds of its clusters, else the throughput kernel
  * (100 + H, GT) with H in 1, 2, 4 (an override (H, GT) maps to the nearest of
- * these); neither code is itself an override (ARX_EINVAL). */
+ * these: (96, 1) to (80, 1), the other cluster shapes to (40, 1)); none of
+ * these codes is itself an override (ARX_EINVAL). */
 int arx_set_launch_shape(int H, int GT);
 
 /* ------------------------------------------------------------ serving ---- */

@@ -143,14 +143,21 @@ constexpr int kCluster16H = 96;
 size_t br_cluster16_smem();
 cudaError_t launch_br_cluster16(const BrArgs &args, int clusters, cudaStream_t st);
 int br_cluster16_occupancy();
+// Shape {kCluster16L2H, 1}: the sixteen-CTA kernel for key sets with gadget
+// l = 2; chosen automatically for such key sets, never by an override.
+constexpr int kCluster16L2H = 80;
+size_t br_cluster16_l2_smem();
+cudaError_t launch_br_cluster16_l2(const BrArgs &args, int clusters, cudaStream_t st);
+int br_cluster16_l2_occupancy();
 inline bool is_cluster_shape(BrShape s) {
-  return s.H == kClusterH || s.H == kCluster4H || s.H == kCluster8H || s.H == kCluster8L2H || s.H == kCluster16H;
+  return s.H == kClusterH || s.H == kCluster4H || s.H == kCluster8H || s.H == kCluster8L2H || s.H == kCluster16H ||
+         s.H == kCluster16L2H;
 }
 // Shapes {kGadget2 + H, GT}: the throughput kernel br_kernel<H, GT, 2> for key
 // sets with gadget l = 2 (H in 1, 2, 4).
 constexpr int kGadget2 = 100;
 // Shapes reserved for key sets with gadget l = 2 (never an override).
-inline bool is_l2_shape(BrShape s) { return s.H == kCluster8L2H || s.H > kGadget2; }
+inline bool is_l2_shape(BrShape s) { return s.H == kCluster8L2H || s.H == kCluster16L2H || s.H > kGadget2; }
 
 // per-shape launchers (one translation unit per H)
 cudaError_t launch_br_h1(const BrArgs &args, int GT, int L, int grid, cudaStream_t st);

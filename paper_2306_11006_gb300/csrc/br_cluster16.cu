@@ -22,10 +22,10 @@
 // then fold the last two stages, run the CRT and update identical copies of
 // ACC_h.  Every
 // cross-CTA dependency is a transaction count on an mbarrier (double-buffered
-// by CMux parity); every wait is bounded.  For the default gadget (l = 3,
-// Bg = 2^7) only: with l = 2 the eight-CTA kernel's four forward warps already
-// have a scheduler each, and the extra exchange partners made this split slower
-// there (measured).
+// by CMux parity); every wait is bounded.  The kernel is a template on the
+// gadget length L: 3 (Bg = 2^7: six forward warps, the inverse pair on warps 3
+// and 4) or 2 (Bg = 2^10, the paper's own set: four forward warps, one per
+// scheduler, the inverse pair on warps 1 and 2).
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -38,10 +38,7 @@ namespace brc16 {
 using namespace clu;
 
 constexpr int kClusterSize = 16;
-constexpr int L = 3;                        // TGSW rows per accumulator component (gadget l = 3)
-constexpr int kCons = 8;                    // six forward warps (two of them the inverse pair), two helpers
-constexpr int kFwd = 2 * L;                 // forward pair of row r: warps r and r + L
-constexpr int kInvWarp = 3;                 // inverse pair: warps 3 and 4 (schedulers 3 and 0)
+constexpr int kCons = 8;                    // forward warps (two of them the inverse pair), helpers
 constexpr int kThreads = (kCons + 1) * 32;  // + producer warp
 constexpr int kConsThreads = kCons * 32;    // 256
 constexpr int kStages = 6;                  // ring of 8 KiB key rows (one prime, both outputs)
@@ -51,7 +48,11 @@ constexpr int kAbarPitch = 640;
 constexpr int kQuarter = 256;
 constexpr uint32_t kPartnerBytes = 7 * kQuarter * 4;  // seven partners, one quarter each
 
+template <int L>  // TGSW rows per accumulator component (gadget length)
 struct Cfg {
+  static constexpr int kFwd = 2 * L;                 // forward pair of row r: warps r and r + L
+  static constexpr int kInvWarp = L == 3 ? 3 : 1;    // inverse pair: warps kInvWarp, kInvWarp + 1
+  static_assert(kInvWarp + 1 < kFwd, "the inverse pair is two of the forward warps");
   static constexpr uint32_t kPeerBytes = L * kQuarter * 4;         // the peer's L row products
   static constexpr size_t kRingBytes = (size_t)kStages * kRowBytes;
   static constexpr size_t kAccBytes = kN * 4;
@@ -69,8 +70,10 @@ struct Cfg {
 };
 
 
+template <int L>
 __global__ void __launch_bounds__(kThreads, 1) br_cluster16_kernel(const __grid_constant__ BrArgs args) {
-  using C = Cfg;  // shared-memory layout
+  using C = Cfg<L>;  // shared-memory layout
+  constexpr int kFwd = C::kFwd, kInvWarp = C::kInvWarp;
   extern __shared__ __align__(128) uint8_t smem[];
   uint32_t *ring = reinterpret_cast<uint32_t *>(smem);  // [stage][output][N]
   uint32_t *A = reinterpret_cast<uint32_t *>(smem + C::kRingBytes);
@@ -149,7 +152,11 @@ __global__ void __launch_bounds__(kThreads, 1) br_cluster16_kernel(const __grid_
     const int rr = fwd ? warp % L : 0;  // forward pairs: row L h + rr on warps rr, rr + L
     const int fw = fwd ? warp / L : 0;  // the warp's half of the pair
     const int tid = threadIdx.x;        // 0 .. 255
-    const PrimeRT pr = prime_rt(P, args.tc);
+    PrimeRT pr = prime_rt(P, args.tc);
+    if (L == 2) {  // first-stage offsets of 10-bit digits
+      pr.dc = args.tc.dig_c2[P];
+      pr.dd = args.tc.dig_d2[P];
+    }
     const uint2 z1 = args.tc.fwd1[P][1], z23 = args.tc.fwd1[P][2 + (Q >> 1)];
     const int jl = 8 * (lane & 3) + (lane >> 2);  // the forward pair's output block (see fwd_quarter_pair)
     const int jf = 32 * fw + jl;
@@ -270,22 +277,24 @@ __global__ void __launch_bounds__(kThreads, 1) br_cluster16_kernel(const __grid_
 }  // namespace brc16
 
 namespace {
+template <int L>
 cudaError_t prepare16() {
   static bool attr = false;  // calls are serialised by the engine lock
   if (attr) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(brc16::br_cluster16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)brc16::Cfg::kSmem);
+  cudaError_t e = cudaFuncSetAttribute(brc16::br_cluster16_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)brc16::Cfg<L>::kSmem);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(brc16::br_cluster16_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    e = cudaFuncSetAttribute(brc16::br_cluster16_kernel<L>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e == cudaSuccess) attr = true;
   return e;
 }
 
+template <int L>
 cudaLaunchConfig_t config16(int clusters, cudaStream_t st, cudaLaunchAttribute *at) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(brc16::kClusterSize * clusters, 1, 1);
   cfg.blockDim = dim3(brc16::kThreads, 1, 1);
-  cfg.dynamicSmemBytes = brc16::Cfg::kSmem;
+  cfg.dynamicSmemBytes = brc16::Cfg<L>::kSmem;
   cfg.stream = st;
   at->id = cudaLaunchAttributeClusterDimension;
   at->val.clusterDim.x = brc16::kClusterSize;
@@ -296,24 +305,26 @@ cudaLaunchConfig_t config16(int clusters, cudaStream_t st, cudaLaunchAttribute *
   return cfg;
 }
 
+template <int L>
 cudaError_t launch16(const BrArgs &args, int clusters, cudaStream_t st) {
-  cudaError_t e = prepare16();
+  cudaError_t e = prepare16<L>();
   if (e != cudaSuccess) return e;
   cudaLaunchAttribute at;
-  cudaLaunchConfig_t cfg = config16(clusters, st, &at);
-  return cudaLaunchKernelEx(&cfg, brc16::br_cluster16_kernel, args);
+  cudaLaunchConfig_t cfg = config16<L>(clusters, st, &at);
+  return cudaLaunchKernelEx(&cfg, brc16::br_cluster16_kernel<L>, args);
 }
 
 // Co-resident sixteen-CTA clusters (0 where the device does not allow them).
+template <int L>
 int occupancy16() {
-  if (prepare16() != cudaSuccess) {
+  if (prepare16<L>() != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
   cudaLaunchAttribute at;
-  cudaLaunchConfig_t cfg = config16(1, nullptr, &at);
+  cudaLaunchConfig_t cfg = config16<L>(1, nullptr, &at);
   int clusters = 0;
-  if (cudaOccupancyMaxActiveClusters(&clusters, brc16::br_cluster16_kernel, &cfg) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveClusters(&clusters, brc16::br_cluster16_kernel<L>, &cfg) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
@@ -321,10 +332,15 @@ int occupancy16() {
 }
 }  // namespace
 
-size_t br_cluster16_smem() { return brc16::Cfg::kSmem; }
+size_t br_cluster16_smem() { return brc16::Cfg<3>::kSmem; }
 cudaError_t launch_br_cluster16(const BrArgs &args, int clusters, cudaStream_t st) {
-  return launch16(args, clusters, st);
+  return launch16<3>(args, clusters, st);
 }
-int br_cluster16_occupancy() { return occupancy16(); }
+int br_cluster16_occupancy() { return occupancy16<3>(); }
+size_t br_cluster16_l2_smem() { return brc16::Cfg<2>::kSmem; }
+cudaError_t launch_br_cluster16_l2(const BrArgs &args, int clusters, cudaStream_t st) {
+  return launch16<2>(args, clusters, st);
+}
+int br_cluster16_l2_occupancy() { return occupancy16<2>(); }
 
 }  // namespace arx

@@ -81,6 +81,7 @@ int ensure_init(Engine &E) {
   E.sms = prop.multiProcessorCount;
   E.policy.sms = E.sms;
   E.policy.clusters16 = E.policy.occupancy(BrShape{kCluster16H, 1});
+  E.policy.clusters16l2 = E.policy.occupancy(BrShape{kCluster16L2H, 1});
   E.policy.clusters8 = E.policy.occupancy(BrShape{kCluster8H, 1});
   E.policy.clusters4 = E.policy.occupancy(BrShape{kCluster4H, 1});
   E.policy.clusters2 = E.policy.occupancy(BrShape{kClusterH, 1});
@@ -211,8 +212,14 @@ BrShape ShapePolicy::wide(int jobs) const {
 BrShape ShapePolicy::for_gadget(int l, BrShape s, int jobs) const {
   if (l != 2) return s;
   const bool cluster = is_cluster_shape(s);
-  // (the eight-CTA kernel only where the device co-schedules eight-CTA clusters)
-  if (clusters8 > 0 && ((!forced.H && jobs <= 2 * clusters8) || (forced.H && cluster))) return {kCluster8L2H, 1};
+  // (each cluster kernel only where the device co-schedules its clusters)
+  if (!forced.H) {
+    if (clusters16l2 > 0 && jobs <= clusters16l2) return {kCluster16L2H, 1};
+    if (clusters8 > 0 && jobs <= 2 * clusters8) return {kCluster8L2H, 1};
+  } else if (cluster) {
+    if (s.H == kCluster16H && clusters16l2 > 0) return {kCluster16L2H, 1};
+    if (clusters8 > 0) return {kCluster8L2H, 1};
+  }
   if (cluster) s = wide(jobs);
   // rows per warp as close as the 4 rows of l = 2 allow: H 6 -> 4, 3 and 2 -> 2
   switch (s.H) {

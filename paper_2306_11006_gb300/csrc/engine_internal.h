@@ -67,6 +67,7 @@ struct TuneEntry {
 struct ShapePolicy {
   int sms = 0;
   int clusters16 = 0, clusters8 = 0, clusters4 = 0, clusters2 = 0;  // co-resident 16- / 8- / 4- / 2-CTA clusters
+  int clusters16l2 = 0;  // co-resident sixteen-CTA clusters of the l = 2 kernel
   std::vector<TuneEntry> tune;
   int tuned_n = -1;
   std::vector<std::pair<BrShape, int>> occ;
@@ -76,10 +77,12 @@ struct ShapePolicy {
   BrShape wide(int jobs) const;  // the throughput shapes of the heuristic
   BrShape pick(int jobs, int n) const;
   // Key sets with gadget l = 2 (given the shape chosen for l = 3 and the wave's
-  // blind rotations): the eight-CTA kernel of their own while a wave takes at
-  // most two rounds of its clusters (its four forward warps already have a
-  // scheduler each, so the sixteen-CTA split gains nothing), else the throughput
-  // kernel br_kernel<H, GT, 2> on the matching shape.
+  // blind rotations): their own sixteen-CTA kernel while the wave's gates fit
+  // its co-resident clusters, else their eight-CTA kernel while a wave takes at
+  // most two rounds of its clusters, else the throughput kernel
+  // br_kernel<H, GT, 2> on the matching shape.  An override of a cluster shape
+  // maps to the l = 2 kernel of the same cluster size (sixteen), else to the
+  // eight-CTA one.
   BrShape for_gadget(int l, BrShape s, int jobs) const;
   int grid(BrShape s, int jobs);
 };

@@ -235,6 +235,7 @@ size_t br_smem(BrShape s) {
   if (s.H == kCluster8H) return s.GT == 1 ? br_cluster8_smem() : 0;
   if (s.H == kCluster8L2H) return s.GT == 1 ? br_cluster8_l2_smem() : 0;
   if (s.H == kCluster16H) return s.GT == 1 ? br_cluster16_smem() : 0;
+  if (s.H == kCluster16L2H) return s.GT == 1 ? br_cluster16_l2_smem() : 0;
   const int L = s.H > kGadget2 ? 2 : 3, H = s.H > kGadget2 ? s.H - kGadget2 : s.H;
   switch (H) {
     case 1: return br_smem_h1(s.GT, L);
@@ -254,6 +255,7 @@ int br_occupancy(BrShape s) {
   if (s.H == kCluster8H) return s.GT == 1 ? br_cluster8_occupancy() : 0;
   if (s.H == kCluster8L2H) return s.GT == 1 ? br_cluster8_l2_occupancy() : 0;
   if (s.H == kCluster16H) return s.GT == 1 ? br_cluster16_occupancy() : 0;
+  if (s.H == kCluster16L2H) return s.GT == 1 ? br_cluster16_l2_occupancy() : 0;
   const int L = s.H > kGadget2 ? 2 : 3, H = s.H > kGadget2 ? s.H - kGadget2 : s.H;
   switch (H) {
     case 1: return br_occupancy_h1(s.GT, L);
@@ -272,6 +274,7 @@ cudaError_t launch_br(const BrArgs &args, BrShape s, int grid, cudaStream_t st) 
   if (s.H == kCluster8H) return s.GT == 1 ? launch_br_cluster8(args, grid, st) : cudaErrorInvalidValue;
   if (s.H == kCluster8L2H) return s.GT == 1 ? launch_br_cluster8_l2(args, grid, st) : cudaErrorInvalidValue;
   if (s.H == kCluster16H) return s.GT == 1 ? launch_br_cluster16(args, grid, st) : cudaErrorInvalidValue;
+  if (s.H == kCluster16L2H) return s.GT == 1 ? launch_br_cluster16_l2(args, grid, st) : cudaErrorInvalidValue;
   const int L = s.H > kGadget2 ? 2 : 3, H = s.H > kGadget2 ? s.H - kGadget2 : s.H;
   switch (H) {
     case 1: return launch_br_h1(args, s.GT, L, grid, st);

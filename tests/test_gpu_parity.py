@@ -409,7 +409,8 @@ def test_gadget_l2_netlist_and_shapes(O, keys512_l2, _loaded512_l2, mode):
     ct = k.encrypt(O, I, bits, 421)
     out = np.zeros((len(nl.outputs), 513), np.uint32)
     with arx.Plan(nl, keyset=ks, mode=mode) as p:
-        assert all((H, GT) == (40, 1) for H, GT, j in p.shapes() if j)
+        sh = [(H, GT) for H, GT, j in p.shapes() if j]
+        assert set(sh) <= {(80, 1), (40, 1)} and (80, 1) in sh, sh  # the l = 2 cluster kernels
         p.run(ct, out)
     assert np.array_equal(out, k.ctx.eval_netlist(nl, ct))
     assert np.array_equal(arx.client_decrypt(512, k.s, out), nl.plain_eval(bits))
@@ -464,14 +465,38 @@ def test_gadget_l2_wide_netlist_takes_the_throughput_kernel(O, keys512_l2, _load
     out = np.zeros((len(nl.outputs), 513), np.uint32)
     with arx.Plan(nl, keyset=ks, mode=arx.MODE_GRAPH) as p:
         sh = p.shapes()
-        assert any(H > 100 for H, GT, j in sh if j > 30) and all(H == 40 for H, GT, j in sh if 0 < j <= 30)
+        assert any(H > 100 for H, GT, j in sh if j > 30) and all(H in (80, 40) for H, GT, j in sh if 0 < j <= 30)
+        assert all(H == 40 for H, GT, j in sh if 16 <= j <= 30) and any(H == 80 for H, GT, j in sh if 0 < j <= 7)
         p.run(ct, out)
         assert _sampled_gate_parity(O, k, nl, p, per_level=4, levels=6) >= 6
     assert np.array_equal(arx.client_decrypt(512, k.s, out), nl.plain_eval(bits))
 
 
+@pytest.mark.parametrize("count", [1, 7, 20])
+def test_gadget_l2_sixteen_cta_kernel(O, keys512_l2, _loaded512_l2, count):
+    # the sixteen-CTA kernel of the gadget l = 2 (shape (80, 1)): one wave of up
+    # to 7 gates by the automatic choice; 20 gates through the (96, 1) override,
+    # which maps to it and takes three rounds of its clusters
+    k, ks = keys512_l2, _loaded512_l2
+    types = np.array([I.BINARY_OPS[j % 6] if j % 5 else I.MUX for j in range(count)], np.uint8)
+    xs, ys, zs = (I.random_bits(460 + j, count) for j in range(3))
+    ca, cb, cc = (k.encrypt(O, I, v, 463 + j) for j, v in enumerate((xs, ys, zs)))
+    out = np.zeros_like(ca)
+    try:
+        if count > 7:
+            arx.set_launch_shape(96, 1)
+        arx.bootstrap_gates_ex(types, ca, cb, cc, out, keyset=ks)
+        nl = I.union([I.ripple_carry_adder(2)])
+        with arx.Plan(nl, keyset=ks, mode=arx.MODE_PLAIN) as p:
+            assert all((H, GT) == (80, 1) for H, GT, j in p.shapes() if j)
+    finally:
+        arx.set_launch_shape(0, 0)
+    assert np.array_equal(out, k.ctx.gates(types, ca, cb, cc))
+    assert np.array_equal(arx.client_decrypt(512, k.s, out), _truth(types, xs, ys, zs))
+
+
 def test_gadget_l2_shape_is_not_an_override(gpu630):
-    for H, GT in ((40, 1), (101, 6), (104, 1)):
+    for H, GT in ((40, 1), (80, 1), (101, 6), (104, 1)):
         with pytest.raises(arx.ArxError):
             arx.set_launch_shape(H, GT)
     with pytest.raises(arx.ArxError):
