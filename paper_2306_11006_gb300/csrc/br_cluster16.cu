@@ -69,7 +69,6 @@ struct Cfg {
                                   kPostBytes + kScrBytes + kPairBytes + kAbarBytes + kBarBytes;
 };
 
-
 template <int L>
 __global__ void __launch_bounds__(kThreads, 1) br_cluster16_kernel(const __grid_constant__ BrArgs args) {
   using C = Cfg<L>;  // shared-memory layout
