@@ -2,7 +2,7 @@
 """Benchmark: gate bootstraps per second of CGGI gate bootstrapping on GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl arx|reference]
-                    [--workload netlists|gates64|dag|matmul] [--mode graph|plain]
+                    [--workload netlists|gates|dag|matmul|simon|serve|alu] [--mode graph|plain]
 
 A step is one evaluation of the workload's netlist through the C-ABI
 (arx_plan_run): every wave's blind rotations (mod switch, n CMux external
@@ -16,21 +16,33 @@ value   = bootstraps per step (MUX counts two) / mean device time per step,
 e2e     = the same through the C-ABI with pinned HOST buffers (H2D of the inputs,
           D2H of the outputs inside the timed region);
 latency = p50 / p99 of the per-step device time (netlist latency);
-roofline= the blind-rotation kernel's modular multiplications per second against
+roofline= the blind-rotation kernels' modular multiplications per second against
           the IMAD-pipe peak (an integer-ALU roofline);
-cpu_baseline = the plain C oracle timed on this host's cores on a bounded sample.
-With --impl reference the oracle itself is the timed arm.
-Under torchrun (N > 1) every rank evaluates its own replica on its own GPU (no
-collective on the data path); value sums all ranks, time is the max over ranks.
+batched / served = the default line also carries the batched-persistent figure
+          (random levelized DAG of 65,536 gates, one CUDA graph) and the served
+          figure (4 clients with their own keys, Poisson arrivals), each with its
+          own roofline fraction and clocks (--no-extra leaves them out);
+cpu_baseline = the plain C oracle on this host's cores evaluating the WHOLE
+          netlist once with the same keys and inputs; every wire of the GPU run
+          (inputs, all gate outputs) is compared with the oracle's bit for bit,
+          and that comparison is part of `verified`.
+With --impl reference the oracle itself is the timed arm: its K timed steps are
+K consecutive slices of the netlist's waves, so that together they evaluate the
+whole netlist once (about 20 s on 16 cores), each slice on the previous slices'
+outputs.  Under torchrun (N > 1) every rank evaluates its own replica on its own
+GPU (no collective on the data path); value sums all ranks, time is the max over
+ranks.
 """
 from __future__ import annotations
 
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -65,6 +77,12 @@ TRAFFIC_PER_LAUNCH = {
     "br_cluster8_kernel<L=2>": 33.68e6 + 6.40e6,  # 8 gates, n = 512, l = 2
     "br_kernel<4,1,L=2>": 34.23e6 + 3.58e6,       # 128 gates, n = 512, l = 2
 }
+KERNEL_OF_H = {12: "br_cluster_kernel", 24: "br_cluster4_kernel", 48: "br_cluster8_kernel",
+               40: "br_cluster8_kernel<L=2>", 80: "br_cluster16_kernel<L=2>", 96: "br_cluster16_kernel"}
+
+
+def kernel_name(H: int, GT: int) -> str:
+    return KERNEL_OF_H.get(H, f"br_kernel<{H - 100},{GT},L=2>" if H > 100 else f"br_kernel<{H},{GT}>")
 
 
 def replica_max_ms(ms: float, world: int, device="cpu") -> float:
@@ -115,15 +133,18 @@ def workload(name: str, gates: int = 64, blocks: int = 8, copies: int = 1):
 
 
 class Clocks:
-    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region
+    (the samples go to a temporary file that is removed once read)."""
 
-    def __init__(self, gpu: int, path: str):
-        self.path, self.proc = path, None
+    def __init__(self, gpu: int):
+        self.proc = None
+        fd, self.path = tempfile.mkstemp(prefix="arx_clocks_", suffix=".csv")
+        os.close(fd)
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
-            self.f = open(path, "w")
+            self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu), f"--query-gpu={q}",
                                           "--format=csv,noheader,nounits", "-lms", "200"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
@@ -132,6 +153,9 @@ class Clocks:
 
     def stop(self):
         if not self.proc:
+            if getattr(self, "f", None):
+                self.f.close()
+            os.unlink(self.path)
             return None
         self.proc.terminate()
         try:
@@ -141,7 +165,10 @@ class Clocks:
         self.f.close()
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        with open(self.path) as f:
+            lines = f.readlines()
+        os.unlink(self.path)
+        for line in lines:
             p = [x.strip() for x in line.split(",")]
             if len(p) < 9:
                 continue
@@ -159,81 +186,286 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def cpu_baseline(nl, budget_s: float = 20.0, n: int = LWE_N, l: int = 3):
-    """The plain C oracle on this host's cores, on a bounded sample of the workload's
-    bootstrapped gates (random inputs), in bootstraps per second."""
-    from oracle import oracle as O
+def cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+        out = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.machine()
 
+
+# ---------------------------------------------------------------------------
+# the oracle leg (CPU): the timed baseline and the bit-exact check of the GPU run
+# ---------------------------------------------------------------------------
+def all_wires(nl):
+    """The same netlist with every wire (inputs and gate outputs) as an output."""
+    W = nl.num_inputs + nl.num_gates
+    return I.Netlist(nl.num_inputs, nl.type, nl.in0, nl.in1, nl.in2, np.arange(W, dtype=np.uint32), nl.name)
+
+
+def wave_slices(waves: np.ndarray, k: int):
+    """Gate ids of k consecutive groups of waves (wave order, gate order inside a wave)."""
+    depth = int(waves.max()) + 1 if len(waves) else 0
+    order = np.argsort(waves, kind="stable")
+    bounds = [round(j * depth / k) for j in range(k + 1)]
+    w = waves[order]
+    return [order[(w >= bounds[j]) & (w < bounds[j + 1])] for j in range(k)]
+
+
+def slice_netlist(nl, gates: np.ndarray):
+    """One slice of gates as a netlist of its own: every wire of the full netlist is
+    an input of the slice, except the slice's own gate outputs, which become its
+    gates (wire W + j for the slice's j-th gate, W = all wires); outputs = the
+    slice's gates.  Pure re-indexing, no arithmetic."""
+    W = nl.num_inputs + nl.num_gates
+    pos = np.full(W, -1, np.int64)
+    pos[nl.num_inputs + gates] = np.arange(len(gates))
+
+    def remap(ids):
+        ids = np.asarray(ids, np.int64)[gates]
+        p = pos[ids]
+        return np.where(p >= 0, W + p, ids).astype(np.uint32)
+
+    return I.Netlist(W, np.asarray(nl.type)[gates], remap(nl.in0), remap(nl.in1), remap(nl.in2),
+                     np.arange(W, W + len(gates), dtype=np.uint32), f"{nl.name}[slice]")
+
+
+def oracle_inputs(nl, n: int, l: int, rank: int = 0):
+    """Oracle key context and input ciphertexts from the same seeded randomness as
+    the GPU arm (keys seed 0; bits and encryption seeds 1000 / 2000 + rank)."""
+    from oracle import oracle as O
     kr = I.key_randomness(0, n, l=l)
     bsk, ksk = O.keygen(kr)
     ctx = O.Context(n, bsk, ksk)
-    cores = os.cpu_count() or 1
-    types = np.array([t for t in nl.type if I.BOOTSTRAPS[int(t)]], np.uint8)
-    if len(types) == 0:
-        types = np.array([I.NAND], np.uint8)
-    rng = np.random.default_rng(7)
-    done, boots, t0 = 0, 0, time.perf_counter()
-    batch = max(cores, 8)
-    while time.perf_counter() - t0 < budget_s / 2 or done == 0:
-        ts = types[rng.integers(0, len(types), batch)]
-        cts = []
-        for k in range(3):
-            m, e = I.encryption_randomness(100 + done + k, batch, n)
-            cts.append(O.encrypt(n, kr.s, m, e, I.random_bits(200 + done + k, batch)))
-        ctx.gates(ts, *cts, nthreads=cores)
-        done += batch
-        boots += int(sum(I.BOOTSTRAPS[int(t)] for t in ts))
+    bits = I.random_bits(replica_seed(1000, rank), nl.num_inputs)
+    m, e = I.encryption_randomness(replica_seed(2000, rank), nl.num_inputs, n)
+    return O, kr, ctx, bits, O.encrypt(n, kr.s, m, e, bits)
+
+
+def single_core_rate(O, ctx, nl, wires, n: int, gates: int = 8):
+    """Oracle on one thread: the first `gates` bootstrapped gates of the netlist on
+    their (oracle-computed) input wires."""
+    g = np.array([k for k in range(nl.num_gates) if I.BOOTSTRAPS[int(nl.type[k])]][:gates], np.int64)
+    if len(g) == 0:
+        return None
+    a, b, c = (wires[np.asarray(x, np.int64)[g]] for x in (nl.in0, nl.in1, nl.in2))
+    t0 = time.perf_counter()
+    ctx.gates(np.asarray(nl.type)[g].astype(np.uint8), a, b, c, nthreads=1)
     dt = time.perf_counter() - t0
-    return {"value": boots / dt, "unit": "bootstraps/s", "cores": cores, "kind": "oracle",
-            "sample": f"{done} gates ({boots} bootstraps) drawn from the workload's gate types, "
-                      f"n={n}, {dt:.1f} s on {cores} threads"}
+    boots = int(sum(I.BOOTSTRAPS[int(t)] for t in np.asarray(nl.type)[g]))
+    return {"value": boots / dt, "unit": "bootstraps/s", "cores": 1,
+            "sample": f"the netlist's first {len(g)} bootstrapped gates on one thread, {dt:.1f} s"}
+
+
+def oracle_leg(nl, n: int, l: int, gpu_wires=None, sample_gates: int = 48):
+    """The plain C oracle on this host's cores.  Small netlists (config 2) are
+    evaluated in full with every wire kept, timed, and -- given gpu_wires(ids), a
+    reader of the GPU run's wires -- compared bit for bit, every wire.  Large
+    netlists are sampled: `sample_gates` gates drawn from the netlist, each
+    evaluated by the oracle on the GPU run's input wires and compared with the
+    GPU's output wire (and timed)."""
+    cores = os.cpu_count() or 1
+    O, kr, ctx, bits, ct_in = oracle_inputs(nl, n, l)
+    boots_total = nl.num_bootstraps
+    rec = {"unit": "bootstraps/s", "cores": cores, "kind": "oracle", "cpu_model": cpu_model()}
+    if boots_total <= 2048:
+        full = all_wires(nl)
+        t0 = time.perf_counter()
+        wires = ctx.eval_netlist(full, ct_in, nthreads=cores)
+        dt = time.perf_counter() - t0
+        rec.update({"value": boots_total / dt, "seconds": dt,
+                    "sample": f"the whole netlist ({nl.num_gates} gates, {boots_total} bootstraps) evaluated "
+                              f"once wave by wave, {dt:.1f} s on {cores} threads"})
+        sc = single_core_rate(O, ctx, nl, wires, n)
+        if sc:
+            rec["single_core"] = sc
+        ok_dec = bool(np.array_equal(O.decrypt(n, kr.s, wires[nl.outputs])[0], nl.plain_eval(bits)))
+        check = {"wires_compared": None, "mismatched": None, "oracle_outputs_decrypt_ok": ok_dec}
+        if gpu_wires is not None:
+            got = gpu_wires(np.arange(len(wires), dtype=np.uint32))
+            bad = int(np.count_nonzero(np.any(got != wires, axis=1)))
+            check.update({"wires_compared": int(len(wires)), "mismatched": bad})
+        return rec, check
+    # sampled form (large netlists): gates drawn from the netlist, GPU input wires
+    rng = np.random.default_rng(11)
+    boot_gates = np.array([k for k in range(nl.num_gates) if I.BOOTSTRAPS[int(nl.type[k])]], np.int64)
+    g = np.sort(rng.choice(boot_gates, size=min(sample_gates, len(boot_gates)), replace=False))
+    rec_check = {"wires_compared": 0, "mismatched": None}
+    if gpu_wires is None:
+        return None, rec_check
+    a, b, c = (gpu_wires(np.asarray(x, np.uint32)[g]) for x in (nl.in0, nl.in1, nl.in2))
+    t0 = time.perf_counter()
+    got = ctx.gates(np.asarray(nl.type)[g].astype(np.uint8), a, b, c, nthreads=cores)
+    dt = time.perf_counter() - t0
+    boots = int(sum(I.BOOTSTRAPS[int(t)] for t in np.asarray(nl.type)[g]))
+    rec.update({"value": boots / dt, "seconds": dt,
+                "sample": f"{len(g)} gates drawn from the netlist, each on the GPU run's input wires, "
+                          f"{dt:.1f} s on {cores} threads"})
+    bad = int(np.count_nonzero(np.any(got != gpu_wires((nl.num_inputs + g).astype(np.uint32)), axis=1)))
+    return rec, {"wires_compared": int(len(g)), "mismatched": bad}
 
 
 def run_reference(args, nl, desc):
+    """The oracle as the timed arm: the K timed steps are K consecutive slices of the
+    netlist's waves (wave order), each evaluated on the previous slices' outputs, so
+    the K steps together evaluate the whole netlist once; W warm-up steps evaluate
+    the first W slices beforehand (untimed)."""
     n, l = (512, 2) if args.paper_params else (LWE_N, 3)
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    for _ in range(args.warmup):
-        cpu_baseline(nl, budget_s=2.0, n=n, l=l)
-    vals = [cpu_baseline(nl, budget_s=max(4.0, 60.0 / max(args.steps, 1)), n=n, l=l) for _ in range(args.steps)]
-    v = statistics.mean(x["value"] for x in vals)
-    boots = sum(I.BOOTSTRAPS[int(t)] for t in nl.type)
+    cores = os.cpu_count() or 1
+    O, kr, ctx, bits, ct_in = oracle_inputs(nl, n, l)
+    _, waves = O.levelize(nl)
+    K = max(args.steps, 1)
+    slices = [slice_netlist(nl, g) for g in wave_slices(waves, K)]
+    gates_of = wave_slices(waves, K)
+    W = nl.num_inputs + nl.num_gates
+
+    def fresh():
+        w = np.zeros((W, n + 1), np.uint32)
+        w[: nl.num_inputs] = ct_in
+        return w
+
+    wires = fresh()
+    for j in range(min(args.warmup, K)):  # warm-up: the first slices, untimed
+        if len(gates_of[j]):
+            wires[nl.num_inputs + gates_of[j]] = ctx.eval_netlist(slices[j], wires, nthreads=cores)
+    wires = fresh()
+    step_s = []
+    for j in range(K):
+        t0 = time.perf_counter()
+        if len(gates_of[j]):
+            wires[nl.num_inputs + gates_of[j]] = ctx.eval_netlist(slices[j], wires, nthreads=cores)
+        step_s.append(time.perf_counter() - t0)
+    total = sum(step_s)
+    boots = nl.num_bootstraps
+    ok = bool(np.array_equal(O.decrypt(n, kr.s, wires[nl.outputs])[0], nl.plain_eval(bits)))
+    v = boots / total
+    sc = single_core_rate(O, ctx, nl, wires, n)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "bootstraps/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * boots / v,
+            "steps": K, "warmup": args.warmup, "ms_per_step": 1000.0 * total / K,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-            "data": "synthetic", "config": {"workload": desc, "lwe_n": n, "gadget": f"l={l}"},
-            "cpu_baseline": {"kind": "oracle", "cores": vals[0]["cores"], "sample": vals[0]["sample"], "value": v},
+            "data": "synthetic",
+            "config": {"workload": desc, "lwe_n": n, "N": 1024, "gadget": f"l={l}, Bg=2^{7 if l == 3 else 10}",
+                       "gates": nl.num_gates, "bootstraps_per_step": boots,
+                       "waves": int(waves.max()) + 1 if len(waves) else 0,
+                       "step": f"1/{K} of the netlist's waves in order; the {K} timed steps together are one "
+                               f"full evaluation ({total:.1f} s)"},
+            "latency_ms": {"full_netlist": 1000.0 * total},
+            "verified": ok,
+            "cpu_baseline": {"kind": "oracle", "cores": cores, "cpu_model": cpu_model(), "value": v,
+                             "sample": f"the whole netlist ({boots} bootstraps) evaluated once, split over the "
+                                       f"{K} timed steps, {total:.1f} s on {cores} threads",
+                             "single_core": sc},
             "e2e": {"value": v, "unit": "bootstraps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def serve_request_pool(count: int, clients: int, seed: int = 5):
-    """Seeded request mix: 32-bit adder, 8x8 multiplier, 16-bit comparator, random
-    DAG with a log-uniform gate count in [1k, 50k]; client c = request % clients."""
-    rng = np.random.default_rng(seed)
-    pool = []
-    for r in range(count):
-        kind = int(rng.integers(0, 4))
-        if kind == 0:
-            nl = I.ripple_carry_adder(32)
-        elif kind == 1:
-            nl = I.array_multiplier(8)
-        elif kind == 2:
-            nl = I.comparator(16)
-        else:
-            g = int(np.exp(rng.uniform(np.log(1000), np.log(50000))))
-            levels = 20
-            wmin = max(8, g // 80)
-            wmax = max(2 * wmin, g // 8)
-            g = min(max(g, wmin * levels), wmax * levels)
-            nl = I.random_dag(seed=1000 + r, total=g, levels=levels, num_inputs=max(64, g // 20), wmin=wmin,
-                              wmax=wmax)
-        pool.append((r % clients, nl))
-    return pool
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def measure_plan(arx, torch, nl, desc, args, n, l, keyset, kr, dev, stream, steps, warmup, mode, world=1,
+                 rank=0, e2e=True):
+    """Times `steps` evaluations of one plan (after `warmup`), L2 flushed between
+    steps; returns the record and the plan (still open) with its inputs."""
+    bits = I.random_bits(replica_seed(1000, rank), nl.num_inputs)
+    m, e = I.encryption_randomness(replica_seed(2000, rank), nl.num_inputs, n)
+    ct_host = arx.client_encrypt(n, kr.s, m, e, bits)
+    ct_in = torch.from_numpy(ct_host.view(np.int32)).to(dev)
+    out = torch.zeros((len(nl.outputs), n + 1), dtype=torch.int32, device=dev)
+    plan = arx.Plan(nl, keyset=keyset, mode=mode)
+    boots = plan.bootstraps
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(max(warmup, 1)):
+        plan.run(ct_in, out, stream)
+    torch.cuda.synchronize(dev)
+    truth = nl.plain_eval(bits)
+    verified = bool(np.array_equal(arx.client_decrypt(n, kr.s, out.cpu().numpy().view(np.uint32)), truth))
+
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    clocks = Clocks(dev.index or 0)
+    for k in range(steps):
+        flush.zero_()
+        evs[k][0].record(stream)
+        plan.run(ct_in, out, stream)
+        evs[k][1].record(stream)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = replica_max_ms(sum(step_ms), world, dev)
+    ok = verified and np.array_equal(arx.client_decrypt(n, kr.s, out.cpu().numpy().view(np.uint32)), truth)
+
+    rec_e2e = None
+    if e2e:  # end to end through the C-ABI with pinned host buffers
+        host_in = torch.from_numpy(ct_host.view(np.int32).copy()).pin_memory()
+        host_out = torch.zeros((len(nl.outputs), n + 1), dtype=torch.int32).pin_memory()
+        e2e_s = []
+        for k in range(steps):
+            flush.zero_()
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            plan.run(host_in, host_out)
+            e2e_s.append(time.perf_counter() - t0)
+        ok = ok and np.array_equal(arx.client_decrypt(n, kr.s, host_out.numpy().view(np.uint32)), truth)
+        rec_e2e = {"value": boots / statistics.mean(e2e_s), "unit": "bootstraps/s",
+                   "h2d_bytes_per_step": int(nl.num_inputs * (n + 1) * 4),
+                   "d2h_bytes_per_step": int(len(nl.outputs) * (n + 1) * 4),
+                   "p50_ms": 1e3 * float(np.percentile(e2e_s, 50))}
+
+    # roofline of the dominant kernels (blind rotation), timed launch by launch
+    br_ms, ks_ms, br_l, ks_l = plan.profile(ct_in)
+    waves_of = {}
+    for H, GT, jobs in plan.shapes():
+        if jobs:
+            k = kernel_name(H, GT)
+            waves_of[k] = waves_of.get(k, 0) + 1
+    br_kernels = sorted(waves_of, key=lambda k: -waves_of[k])  # dominant (most waves) first
+    achieved = boots * n * modmul_per_cmux(l) / (br_ms / 1e3) / 1e12
+    launches_per_step = br_l + ks_l + (1 if len(nl.outputs) else 0)
+    rec = {
+        "value": replica_value(boots, steps, world, total_ms), "unit": "bootstraps/s", "steps": steps,
+        "warmup": warmup, "ms_per_step": total_ms / steps,
+        "config": {"workload": desc, "lwe_n": n, "N": 1024, "gadget": f"l={l}, Bg=2^{arx.GADGET_BITS[l]}",
+                   "mode": "graph" if mode == arx.MODE_GRAPH else "plain", "shape": args.shape,
+                   "gates": nl.num_gates, "bootstraps_per_step": boots, "waves": plan.waves,
+                   "l2": "flushed between steps (256 MiB write)",
+                   "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
+        "gates_per_s": nl.num_gates * steps * world / (total_ms / 1e3),
+        "verified": bool(ok),
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TMODMUL, "unit": "Tmodmul/s",
+                     "frac": achieved / ALU_PEAK_TMODMUL,
+                     "traffic": TRAFFIC_PER_LAUNCH.get(br_kernels[0]) if br_kernels else None,
+                     "kernel": br_kernels[0] if br_kernels else None,
+                     "waves_per_kernel": waves_of,
+                     "scope": "achieved over all blind-rotation launches of a step",
+                     "kernel_ms_per_step": br_ms, "ks_ms_per_step": ks_ms},
+        "gpu_launches": launches_per_step * steps,
+        "clocks": clk,
+    }
+    if rec_e2e:
+        rec["e2e"] = rec_e2e
+    return rec, plan
 
 
-def run_serve(args):
+def run_serve(args, record_only=False):
+    """Served throughput: `clients` key sets, Poisson arrivals of a seeded request
+    mix, continuous batching in the library's server."""
     import torch
 
     from paper_2306_11006_gb300 import arx
@@ -264,8 +496,7 @@ def run_serve(args):
     base = srv.stats()
     rng = np.random.default_rng(9)
     arrivals = np.cumsum(rng.exponential(1.0 / args.rate, len(pool)))
-    clocks = Clocks(local, os.path.join(ROOT, "gpurun_out", "clocks_serve.csv")) \
-        if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else Clocks(local, "/tmp/arx_clocks_serve.csv")
+    clocks = Clocks(local)
     ids = []
     t0 = time.perf_counter()
     for (c, nl), (bits, ct), at in zip(pool, inputs, arrivals):
@@ -284,31 +515,59 @@ def run_serve(args):
     gates = st["gates"] - base["gates"]
     busy = st["busy_s"] - base["busy_s"]
     achieved = boots * n * MODMUL_PER_CMUX / max(busy, 1e-9) / 1e12
-    line = {
-        "metric": METRIC, "value": boots / elapsed, "unit": "bootstraps/s", "n_gpus": world,
-        "steps": len(pool), "warmup": len(warm), "ms_per_step": 1e3 * elapsed / len(pool),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+    for _, ks in keys:
+        arx.unload_keys(ks)
+    rec = {
+        "value": boots / elapsed, "unit": "bootstraps/s", "steps": len(pool), "warmup": len(warm),
+        "ms_per_step": 1e3 * elapsed / len(pool),
         "config": {"workload": f"serving: {args.clients} clients, Poisson {args.rate}/s, {len(pool)} requests "
                                "(adder32 | mult8 | cmp16 | random DAG 1k-50k gates)", "lwe_n": n,
                    "arrival_rate": args.rate, "clients": args.clients},
         "latency_ms": {"p50": st["p50_ms"], "p99": st["p99_ms"]},
         "gates_per_s": gates / elapsed, "verified": bool(ok),
         "serve": {"requests": len(pool), "bootstraps": int(boots), "gates": int(gates), "elapsed_s": elapsed,
-                  "busy_s": busy, "ticks": int(st["ticks"] - base["ticks"]), "launches": int(st["launches"] - base["launches"]),
-                  "peak_active": int(st["peak_active"])},
-        "e2e": {"value": boots / elapsed, "unit": "bootstraps/s",
-                "h2d_bytes_per_step": int(np.mean([nl.num_inputs for _, nl in pool]) * (n + 1) * 4),
-                "d2h_bytes_per_step": int(np.mean([len(nl.outputs) for _, nl in pool]) * (n + 1) * 4)},
+                  "busy_s": busy, "ticks": int(st["ticks"] - base["ticks"]),
+                  "launches": int(st["launches"] - base["launches"]), "peak_active": int(st["peak_active"])},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TMODMUL, "unit": "Tmodmul/s",
                      "frac": achieved / ALU_PEAK_TMODMUL, "traffic": None,
-                     "kernel": "br_kernel + ks_kernel over the server's busy time"},
+                     "kernel": "all blind rotations of the run over the server's busy time"},
         "gpu_launches": int(st["launches"] - base["launches"]),
         "clocks": clk,
     }
-    for _, ks in keys:
-        arx.unload_keys(ks)
+    if record_only:
+        return rec
+    line = {"metric": METRIC, "n_gpus": world, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u32", "data": "synthetic", **rec,
+            "e2e": {"value": boots / elapsed, "unit": "bootstraps/s",
+                    "h2d_bytes_per_step": int(np.mean([nl.num_inputs for _, nl in pool]) * (n + 1) * 4),
+                    "d2h_bytes_per_step": int(np.mean([len(nl.outputs) for _, nl in pool]) * (n + 1) * 4)}}
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def serve_request_pool(count: int, clients: int, seed: int = 5):
+    """Seeded request mix: 32-bit adder, 8x8 multiplier, 16-bit comparator, random
+    DAG with a log-uniform gate count in [1k, 50k]; client c = request % clients."""
+    rng = np.random.default_rng(seed)
+    pool = []
+    for r in range(count):
+        kind = int(rng.integers(0, 4))
+        if kind == 0:
+            nl = I.ripple_carry_adder(32)
+        elif kind == 1:
+            nl = I.array_multiplier(8)
+        elif kind == 2:
+            nl = I.comparator(16)
+        else:
+            g = int(np.exp(rng.uniform(np.log(1000), np.log(50000))))
+            levels = 20
+            wmin = max(8, g // 80)
+            wmax = max(2 * wmin, g // 8)
+            g = min(max(g, wmin * levels), wmax * levels)
+            nl = I.random_dag(seed=1000 + r, total=g, levels=levels, num_inputs=max(64, g // 20), wmin=wmin,
+                              wmax=wmax)
+        pool.append((r % clients, nl))
+    return pool
 
 
 def run_alu(args):
@@ -318,8 +577,7 @@ def run_alu(args):
     if int(os.environ.get("RANK", "0")) != 0:
         return
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    clk = Clocks(local, os.path.join(ROOT, "gpurun_out", "clocks_alu.csv")) \
-        if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else Clocks(local, "/tmp/arx_clocks_alu.csv")
+    clk = Clocks(local)
     rates = arx.probe_alu()
     clocks = clk.stop()
     import torch
@@ -344,7 +602,7 @@ def main():
     ap.add_argument("--workload", default="netlists",
                     choices=["netlists", "gates", "gates64", "dag", "matmul", "serve", "alu", "simon"])
     ap.add_argument("--clients", type=int, default=4, help="serve: clients (key sets)")
-    ap.add_argument("--rate", type=float, default=4.0, help="serve: Poisson arrival rate, requests/s")
+    ap.add_argument("--rate", type=float, default=16.0, help="serve: Poisson arrival rate, requests/s")
     ap.add_argument("--requests", type=int, default=32, help="serve: requests per run")
     ap.add_argument("--gates", type=int, default=64, help="gate count of the independent-gates workload")
     ap.add_argument("--blocks", type=int, default=8, help="cipher blocks of the simon workload")
@@ -352,6 +610,7 @@ def main():
     ap.add_argument("--shape", default=None, help="force the blind-rotation launch shape H,GT")
     ap.add_argument("--mode", default="graph", choices=["graph", "plain"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="leave out the batched and served sub-records")
     ap.add_argument("--paper-params", action="store_true",
                     help="the paper's own set: n = 512, gadget l = 2 (Bg = 2^10), instead of n = 630, l = 3")
     args = ap.parse_args()
@@ -362,8 +621,9 @@ def main():
         return run_alu(args)
     if args.workload == "serve":
         if args.impl == "reference":
-            nl, desc = workload("dag")
-            return run_reference(args, nl, "serving request mix (oracle on its gate types)")
+            print(json.dumps({"impl": "reference", "unavailable": "the oracle has no server; its netlist "
+                                                                  "throughput is the default workload's line"}))
+            return
         return run_serve(args)
     nl, desc = workload(args.workload, args.gates, args.blocks, args.copies)
     if args.impl == "reference":
@@ -388,101 +648,34 @@ def main():
     kr = I.key_randomness(0, n, l=l)
     bsk, ksk = arx.client_keygen(kr)
     keyset = arx.load_keys(bsk, ksk, n, l=l)
-    bits = I.random_bits(replica_seed(1000, rank), nl.num_inputs)
-    m, e = I.encryption_randomness(replica_seed(2000, rank), nl.num_inputs, n)
-    ct_host = arx.client_encrypt(n, kr.s, m, e, bits)
-    ct_in = torch.from_numpy(ct_host.view(np.int32)).to(dev)
-    out = torch.zeros((len(nl.outputs), n + 1), dtype=torch.int32, device=dev)
     mode = arx.MODE_GRAPH if args.mode == "graph" else arx.MODE_PLAIN
     if args.shape:
         H, GT = (int(v) for v in args.shape.split(","))
         arx.set_launch_shape(H, GT)
-    plan = arx.Plan(nl, keyset=keyset, mode=mode)
-    boots = plan.bootstraps
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-
-    for _ in range(max(args.warmup, 1)):
-        plan.run(ct_in, out, stream)
-    torch.cuda.synchronize(dev)
-    truth = nl.plain_eval(bits)
-    verified = bool(np.array_equal(arx.client_decrypt(n, kr.s, out.cpu().numpy().view(np.uint32)), truth))
-
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize(dev)
-    clocks = Clocks(local, os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")) \
-        if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else Clocks(local, f"/tmp/arx_clocks_{rank}.csv")
-    for k in range(args.steps):
-        flush.zero_()
-        evs[k][0].record(stream)
-        plan.run(ct_in, out, stream)
-        evs[k][1].record(stream)
-    torch.cuda.synchronize(dev)
-    if world > 1:
-        dist.barrier()
-    clk = clocks.stop()
-    step_ms = [a.elapsed_time(b) for a, b in evs]
-    total_ms = sum(step_ms)
-    total_ms = replica_max_ms(total_ms, world, dev)
-    ok = verified and np.array_equal(
-        arx.client_decrypt(n, kr.s, out.cpu().numpy().view(np.uint32)), truth)
-
-    # end to end through the C-ABI with pinned host buffers
-    host_in = torch.from_numpy(ct_host.view(np.int32).copy()).pin_memory()
-    host_out = torch.zeros((len(nl.outputs), n + 1), dtype=torch.int32).pin_memory()
-    e2e_s = []
-    for k in range(args.steps):
-        flush.zero_()
-        torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        plan.run(host_in, host_out)
-        e2e_s.append(time.perf_counter() - t0)
-    e2e_ok = np.array_equal(arx.client_decrypt(n, kr.s, host_out.numpy().view(np.uint32)), truth)
-
-    # roofline of the dominant kernel (blind rotation), timed launch by launch
-    br_ms, ks_ms, br_l, ks_l = plan.profile(ct_in)
-    waves_of = {}
-    for H, GT, jobs in plan.shapes():
-        if jobs:
-            k = {12: "br_cluster_kernel", 24: "br_cluster4_kernel", 48: "br_cluster8_kernel",
-                 40: "br_cluster8_kernel<L=2>", 80: "br_cluster16_kernel<L=2>", 96: "br_cluster16_kernel"}.get(
-                     H, f"br_kernel<{H - 100},{GT},L=2>" if H > 100 else f"br_kernel<{H},{GT}>")
-            waves_of[k] = waves_of.get(k, 0) + 1
-    br_kernels = sorted(waves_of, key=lambda k: -waves_of[k])  # dominant (most waves) first
-    ops = boots * n * modmul_per_cmux(l)
-    achieved = ops / (br_ms / 1e3) / 1e12
-    launches_per_step = br_l + ks_l + (1 if len(nl.outputs) else 0)
-
-    value = replica_value(boots, args.steps, world, total_ms)
-    line = {
-        "metric": METRIC, "value": value, "unit": "bootstraps/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": desc, "lwe_n": n, "N": 1024, "gadget": f"l={l}, Bg=2^{arx.GADGET_BITS[l]}", "mode": args.mode, "shape": args.shape, "gates": nl.num_gates,
-                   "bootstraps_per_step": boots, "waves": plan.waves,
-                   "l2": "flushed between steps (256 MiB write)", "parallelism": "replicas" if world > 1 else "1 GPU"},
-        "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
-        "gates_per_s": nl.num_gates * args.steps * world / (total_ms / 1e3),
-        "verified": bool(ok and e2e_ok),
-        "e2e": {"value": boots / statistics.mean(e2e_s), "unit": "bootstraps/s",
-                "h2d_bytes_per_step": int(nl.num_inputs * (n + 1) * 4),
-                "d2h_bytes_per_step": int(len(nl.outputs) * (n + 1) * 4),
-                "p50_ms": 1e3 * float(np.percentile(e2e_s, 50))},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TMODMUL, "unit": "Tmodmul/s",
-                     "frac": achieved / ALU_PEAK_TMODMUL,
-                     "traffic": TRAFFIC_PER_LAUNCH.get(br_kernels[0]) if br_kernels else None,
-                     "kernel": br_kernels[0] if br_kernels else None,
-                     "waves_per_kernel": waves_of,
-                     "scope": "achieved over all blind-rotation launches of a step",
-                     "kernel_ms_per_step": br_ms, "ks_ms_per_step": ks_ms},
-        "gpu_launches": launches_per_step * args.steps,
-        "clocks": clk,
-    }
-    plan.close()
-    arx.unload_keys(keyset)
+    rec, plan = measure_plan(arx, torch, nl, desc, args, n, l, keyset, kr, dev, stream, args.steps, args.warmup,
+                             mode, world, rank)
+    line = {"metric": METRIC, "n_gpus": world, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u32", "data": "synthetic", **rec}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(nl, n=n, l=l)
+        # the oracle leg: timed on this host's cores, and the GPU run's wires checked bit for bit
+        cb, check = oracle_leg(nl, n, l, lambda ids: plan.wires(ids, n))
+        if cb:
+            line["cpu_baseline"] = cb
+        line["oracle_check"] = check
+        line["verified"] = bool(line["verified"] and check["mismatched"] == 0)
+    plan.close()
+    # batched-persistent and served figures beside the plain per-level line
+    extra = (rank == 0 and world == 1 and not args.no_extra and args.workload == "netlists"
+             and args.copies == 1 and not args.paper_params and not args.shape)
+    if extra:
+        dag, ddesc = workload("dag")
+        brec, bplan = measure_plan(arx, torch, dag, ddesc + " (batched: one CUDA graph, autotuned shapes)", args,
+                                   n, l, keyset, kr, dev, stream, 3, 1, arx.MODE_GRAPH, e2e=False)
+        bplan.close()
+        line["batched"] = brec
+    arx.unload_keys(keyset)
+    if extra:
+        line["served"] = run_serve(args, record_only=True)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
