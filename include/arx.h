@@ -90,9 +90,11 @@ int arx_load_keys_ex(const uint32_t *bsk, const uint32_t *ksk, int lwe_n, void *
  * forward DFTs per CMux, (k+1) l = 4; Sec. 6 uses n = 512).  The bootstrapping
  * key then has 2 l rows per index: [n][2l][2][N], row r = c*l + (p-1), gadget
  * level p scaled by 2^(32 - p bg_bits).  Key sets with l = 2 run their blind
- * rotations on one kernel of their own (the eight-CTA cluster kernel built for
- * 10-bit digits) whatever the launch-shape override.  ARX_EINVAL for any other
- * gadget. */
+ * rotations on kernels instantiated for 10-bit digits: the sixteen-CTA cluster
+ * kernel for waves that fit its co-resident clusters, the eight-CTA one for
+ * waves of up to two rounds of its clusters, else the throughput kernel with
+ * l = 2 (see arx_set_launch_shape for how an override maps onto them).
+ * ARX_EINVAL for any other gadget. */
 int arx_load_keys_gadget(const uint32_t *bsk, const uint32_t *ksk, int lwe_n, int l, int bg_bits, void *stream);
 
 /* Free a key set.  ARX_EBUSY while a plan references it. */
@@ -109,9 +111,16 @@ size_t arx_resident_bytes(void);
 /* ------------------------------------------------------------ gates ---- */
 
 /* count independent gates: ct_out[g] = types[g](ct_a[g], ct_b[g]) with the
- * default key set.  types: host array of arx_gate (NOT / COPY read ct_a only,
- * CONST read neither; MUX needs arx_bootstrap_gates_ex).  ct_*: [count][n+1].
- * count = 0 is a no-op.  Synchronous. */
+ * default key set.  Each two-input gate is the gate of Fig. 2 (Sec. 2.2): its
+ * linear pre-combination of the inputs, mod switch to 2N, blind rotation by n
+ * CMux external products with the bootstrapping key, sample extraction and the
+ * key switch; NOT / COPY / CONST are linear and not bootstrapped.  All count
+ * gates run as one wave (one blind-rotation launch, one key-switch launch).
+ * types: host array of arx_gate (NOT / COPY read ct_a only, CONST read
+ * neither; MUX needs arx_bootstrap_gates_ex).  ct_*: [count][n+1], host or
+ * device memory; ct_out may alias ct_a or ct_b (inputs are copied to the
+ * device before any output is written).  count = 0 is a no-op; count > 2^24,
+ * a bad type or a NULL input a gate needs: ARX_EINVAL.  Synchronous. */
 int arx_bootstrap_gates(const uint8_t *types, const uint32_t *ct_a, const uint32_t *ct_b,
                         uint32_t *ct_out, size_t count);
 
@@ -140,14 +149,38 @@ typedef struct {
  * *depth receives the number of waves.  ARX_EINVAL / ARX_ECYCLE on bad input. */
 int arx_levelize(const arx_netlist *nl, uint32_t *wave, uint32_t *depth);
 
-/* Evaluate a netlist with the default key set, wave by wave, one blind-rotation
- * launch and one key-switch launch per wave.  ct_in [num_inputs][n+1],
- * ct_out [num_outputs][n+1].  Synchronous. */
+/* The Sec. 4.2 levelization with launch widths evened out (host only, no GPU
+ * needed); graph-mode plans use it.  The depth stays that of arx_levelize, and
+ * each gate g is placed between its earliest level (arx_levelize) and its
+ * latest one (the last level that still leaves one level per gate of its
+ * longest chain of readers), so that every gate still runs after its inputs and
+ * all results equal those of the plain levelization.  Level by level, the gates
+ * whose latest level it is are taken, then more ready gates (earliest latest
+ * level first) while the level's blind rotations (MUX two, NOT / COPY / CONST
+ * none) stay within the free capacity of the launch: caps[0 .. ncaps-1] is an
+ * increasing list of launch capacities (for a GB300, the co-resident 16-, 8-,
+ * 4- and 2-CTA clusters), and a level that must run j blind rotations may be
+ * filled up to the smallest cap >= j (not beyond j when j > every cap).  The
+ * reason: a narrow wave runs one gate per cluster and costs the same for any
+ * count up to the co-resident clusters.  wave[g], *depth as arx_levelize.
+ * ARX_EINVAL / ARX_ECYCLE on bad input or non-increasing caps. */
+int arx_levelize_balanced(const arx_netlist *nl, const uint32_t *caps, uint32_t ncaps, uint32_t *wave,
+                          uint32_t *depth);
+
+/* Evaluate a netlist with the default key set (Sec. 4.2): the gates are
+ * levelized into waves (arx_levelize), and every wave -- all of its ready gates,
+ * of any types -- runs as one blind-rotation launch and one key-switch launch,
+ * waves in order; wires stay on the device between waves.  ct_in
+ * [num_inputs][n+1], ct_out [num_outputs][n+1], host or device memory.  Bad
+ * wire ids or types: ARX_EINVAL; a cycle: ARX_ECYCLE; no key set: ARX_ENOKEYS.
+ * Synchronous. */
 int arx_eval_netlist(const arx_netlist *nl, const uint32_t *ct_in, uint32_t *ct_out);
 
 /* Execution modes of a plan. */
 #define ARX_MODE_PLAIN 0   /* per-wave launches, fixed heuristic shapes */
-#define ARX_MODE_GRAPH 1   /* autotuned persistent shapes, whole plan replayed as one CUDA graph */
+#define ARX_MODE_GRAPH 1   /* autotuned persistent shapes, launch widths balanced within slack
+                              (as arx_levelize_balanced, capacities from the autotuner's
+                              measured launch costs), whole plan replayed as one CUDA graph */
 
 int arx_eval_netlist_ex(const arx_netlist *nl, const uint32_t *ct_in, uint32_t *ct_out, int keyset,
                         int mode, void *stream);

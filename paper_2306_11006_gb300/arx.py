@@ -52,6 +52,7 @@ SIGNATURES = {
     "arx_bootstrap_gates": (_i, [_vp, _vp, _vp, _vp, _sz]),
     "arx_bootstrap_gates_ex": (_i, [_vp, _vp, _vp, _vp, _vp, _sz, _i, _vp]),
     "arx_levelize": (_i, [_NLP, _vp, _vp]),
+    "arx_levelize_balanced": (_i, [_NLP, _vp, _u32, _vp, _vp]),
     "arx_eval_netlist": (_i, [_NLP, _vp, _vp]),
     "arx_eval_netlist_ex": (_i, [_NLP, _vp, _vp, _i, _i, _vp]),
     "arx_plan_create": (_i, [_NLP, _i, _i]),
@@ -201,6 +202,18 @@ def levelize(nl):
     wave = np.zeros(max(len(r.type), 1), np.uint32)
     depth = ctypes.c_uint32(0)
     _check(lib().arx_levelize(r.ref, _ptr(wave), ctypes.addressof(depth)))
+    return wave[: len(r.type)], depth.value
+
+
+def levelize_balanced(nl, caps):
+    """Levels with launch widths evened out within slack (arx_levelize_balanced):
+    caps = increasing launch capacities in blind rotations.  Returns (wave, depth)."""
+    r = _NetlistRef(nl)
+    c = np.ascontiguousarray(np.asarray(caps, dtype=np.uint32))
+    wave = np.zeros(max(len(r.type), 1), np.uint32)
+    depth = ctypes.c_uint32(0)
+    _check(lib().arx_levelize_balanced(r.ref, _ptr(c) if len(c) else None, len(c), _ptr(wave),
+                                       ctypes.addressof(depth)))
     return wave[: len(r.type)], depth.value
 
 

@@ -13,13 +13,16 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
 #include <map>
 #include <memory>
 #include <mutex>
+#include <queue>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/arx.h"
@@ -247,6 +250,33 @@ BrShape ShapePolicy::pick(int jobs, int n) const {
   return out;
 }
 
+int ShapePolicy::free_capacity(int jobs, int n, int l) const {
+  if (jobs <= 0) return 0;
+  if (forced.H) return jobs;
+  if (l == 3 && !tune.empty() && tuned_n == n) {
+    // cost of the best shape for `jobs` (as pick), then the widest launch of any
+    // shape within that cost
+    double best = 1e300;
+    for (const TuneEntry &t : tune)
+      best = std::min(best, ((jobs + t.gates_per_wave - 1) / t.gates_per_wave) * t.wave_ms_per_cmux);
+    long long cap = jobs;
+    for (const TuneEntry &t : tune) {
+      const long long rounds = (long long)(best / t.wave_ms_per_cmux * (1.0 + 1e-9));
+      cap = std::max(cap, rounds * t.gates_per_wave);
+    }
+    return (int)std::min<long long>(cap, INT_MAX / 2);
+  }
+  // the heuristic's cluster classes (rounds of co-resident clusters)
+  const int c16 = l == 2 ? clusters16l2 : clusters16;
+  if (c16 > 0 && jobs <= c16) return c16;
+  if (clusters8 > 0 && jobs <= clusters8) return clusters8;
+  if (l == 2) return clusters8 > 0 && jobs <= 2 * clusters8 ? 2 * clusters8 : jobs;
+  if (clusters4 > 0 && jobs <= clusters4) return clusters4;
+  const int c2 = std::max(clusters2, sms / 2);
+  if (jobs <= c2) return c2;
+  return jobs;
+}
+
 // Grid of a launch: CTAs, or clusters for the cluster shapes.
 int ShapePolicy::grid(BrShape s, int jobs) {
   if (is_cluster_shape(s)) return std::max(1, std::min(jobs, std::max(1, occupancy(s))));
@@ -380,6 +410,74 @@ int levelize(const arx_netlist *nl, uint32_t *wave, uint32_t *depth) {
   return ARX_OK;
 }
 
+// Launch widths within slack.  latest[g] is the last level at which gate g can
+// run without deepening the netlist (depth - 1 for a gate no other gate reads,
+// else one before its earliest reader's latest level).  Level by level, the
+// launch takes every ready gate whose latest level it is, then -- earliest
+// deadline first -- more ready gates while the launch's cost does not grow
+// (cap_of on the blind rotations: MUX two, linear gates none).  By
+// induction a gate's inputs are placed by the level before its latest one, so
+// every gate is placed by its latest level: the depth stays, each gate still
+// runs after its inputs, and the results are those of the paper's levelization.
+void balance_levels(const arx_netlist *nl, uint32_t depth, const std::function<long long(long long)> &cap_of,
+                    uint32_t *wave) {
+  const uint32_t G = nl->num_gates, I = nl->num_inputs;
+  if (!G || depth < 2) return;
+  const uint32_t *ins[3] = {nl->in0, nl->in1, nl->in2};
+  std::vector<uint32_t> start(G + 1, 0), npred(G, 0), weight(G);
+  for (uint32_t g = 0; g < G; ++g) {
+    const uint32_t t = nl->type[g];
+    weight[g] = t == ARX_MUX ? 2u : gate_arity(t) == 2 ? 1u : 0u;
+    for (int s = 0; s < gate_arity(t); ++s)
+      if (ins[s][g] >= I) {
+        npred[g]++;
+        start[ins[s][g] - I + 1]++;
+      }
+  }
+  for (uint32_t g = 0; g < G; ++g) start[g + 1] += start[g];
+  std::vector<uint32_t> succ(start[G]), fill(start.begin(), start.end() - 1);
+  for (uint32_t g = 0; g < G; ++g)
+    for (int s = 0; s < gate_arity(nl->type[g]); ++s)
+      if (ins[s][g] >= I) succ[fill[ins[s][g] - I]++] = g;
+  // latest levels, readers first (by decreasing earliest level)
+  std::vector<uint32_t> by(G), cnt(depth + 1, 0);
+  for (uint32_t g = 0; g < G; ++g) cnt[wave[g] + 1]++;
+  for (uint32_t w = 0; w < depth; ++w) cnt[w + 1] += cnt[w];
+  for (uint32_t g = 0; g < G; ++g) by[cnt[wave[g]]++] = g;
+  std::vector<uint32_t> latest(G, depth - 1);
+  for (uint32_t k = G; k-- > 0;) {
+    const uint32_t g = by[k];
+    for (uint32_t e = start[g]; e < start[g + 1]; ++e) latest[g] = std::min(latest[g], latest[succ[e]] - 1);
+  }
+  typedef std::pair<uint32_t, uint32_t> Item;  // (latest level, gate)
+  std::priority_queue<Item, std::vector<Item>, std::greater<Item>> ready;
+  for (uint32_t g = 0; g < G; ++g)
+    if (!npred[g]) ready.push(Item(latest[g], g));
+  std::vector<uint32_t> taken, next;
+  for (uint32_t L = 0; L < depth; ++L) {
+    taken.clear();
+    long long jobs = 0;
+    while (!ready.empty() && ready.top().first <= L) {  // due now
+      taken.push_back(ready.top().second);
+      jobs += weight[ready.top().second];
+      ready.pop();
+    }
+    const long long cap = jobs > 0 ? cap_of(jobs) : 0;
+    while (!ready.empty() && jobs + weight[ready.top().second] <= cap) {  // free room, earliest deadline first
+      taken.push_back(ready.top().second);
+      jobs += weight[ready.top().second];
+      ready.pop();
+    }
+    next.clear();
+    for (uint32_t g : taken) {
+      wave[g] = L;
+      for (uint32_t e = start[g]; e < start[g + 1]; ++e)
+        if (--npred[succ[e]] == 0) next.push_back(succ[e]);
+    }
+    for (uint32_t g : next) ready.push(Item(latest[g], g));
+  }
+}
+
 // Key-switch scratch: partial sums [jobs][splits][632] and zeroed counters [jobs].
 int reserve_ks_scratch(DevBuf &part, DevBuf &cnt, size_t jobs, int splits) {
   if (splits <= 1 || !jobs) return ARX_OK;
@@ -403,6 +501,17 @@ int plan_build(Engine &E, const arx_netlist *nl, int keyset, int mode, std::uniq
   uint32_t depth = 0;
   rc = levelize(nl, wave.data(), &depth);
   if (rc) return rc;
+  if (mode == ARX_MODE_GRAPH) {  // autotuned shapes, launch widths balanced within slack
+    if (ks->l == 3) {
+      rc = calibrate(E, ks->n);
+      if (rc) return rc;
+    }
+    const ShapePolicy &pol = E.policy;
+    const int n = ks->n, l = ks->l;
+    balance_levels(
+        nl, depth, [&](long long j) { return (long long)pol.free_capacity((int)std::min<long long>(j, INT_MAX / 2), n, l); },
+        wave.data());
+  }
   std::unique_ptr<Plan> P(new Plan);
   P->keyset = keyset < 0 ? E.last : keyset;
   P->n = ks->n;
@@ -421,6 +530,7 @@ int plan_build(Engine &E, const arx_netlist *nl, int keyset, int mode, std::uniq
   std::vector<KsJob> ksj;
   int max_br = 0;
   for (uint32_t w = 0; w < depth; ++w) {
+    if (cnt[w + 1] == cnt[w]) continue;  // a level the balancing emptied
     Level L{};
     L.br_off = (int)br.size();
     L.ks_off = (int)ksj.size();
@@ -437,10 +547,6 @@ int plan_build(Engine &E, const arx_netlist *nl, int keyset, int mode, std::uniq
     P->levels.push_back(L);
   }
   P->bootstraps = br.size();
-  if (mode == ARX_MODE_GRAPH && P->l == 3) {  // the gadget l = 2 has a single kernel
-    rc = calibrate(E, P->n);
-    if (rc) return rc;
-  }
   size_t ks_part_max = 0, ks_gate_max = 0;
   for (Level &L : P->levels) {
     L.shape = E.policy.for_gadget(
@@ -795,6 +901,28 @@ extern "C" int arx_levelize(const arx_netlist *nl, uint32_t *wave, uint32_t *dep
   if (!wave && nl && nl->num_gates) return fail(ARX_EINVAL, "wave is null");
   uint32_t dummy = 0;
   return levelize(nl, wave ? wave : &dummy, depth);
+}
+
+extern "C" int arx_levelize_balanced(const arx_netlist *nl, const uint32_t *caps, uint32_t ncaps, uint32_t *wave,
+                                     uint32_t *depth) {
+  if (!wave && nl && nl->num_gates) return fail(ARX_EINVAL, "wave is null");
+  if (ncaps && !caps) return fail(ARX_EINVAL, "caps is null");
+  for (uint32_t k = 1; k < ncaps; ++k)
+    if (caps[k] <= caps[k - 1]) return fail(ARX_EINVAL, "caps must increase");
+  uint32_t dummy = 0, d = 0;
+  int rc = levelize(nl, wave ? wave : &dummy, &d);
+  if (rc) return rc;
+  if (depth) *depth = d;
+  if (!nl->num_gates) return ARX_OK;
+  balance_levels(
+      nl, d,
+      [&](long long j) {
+        for (uint32_t k = 0; k < ncaps; ++k)
+          if (j <= (long long)caps[k]) return (long long)caps[k];
+        return j;
+      },
+      wave);
+  return ARX_OK;
 }
 
 extern "C" int arx_eval_netlist_ex(const arx_netlist *nl, const uint32_t *ct_in, uint32_t *ct_out, int keyset,

@@ -4,6 +4,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <functional>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -76,6 +77,11 @@ struct ShapePolicy {
   BrShape heuristic(int jobs) const;
   BrShape wide(int jobs) const;  // the throughput shapes of the heuristic
   BrShape pick(int jobs, int n) const;
+  // The most blind rotations one launch takes at the cost of a launch of `jobs`
+  // (gadget length l): a cluster kernel's wave costs the same for every count up
+  // to its co-resident clusters, so the rest of that width is free; with the
+  // autotuned table the costs are the measured ones.
+  int free_capacity(int jobs, int n, int l) const;
   // Key sets with gadget l = 2 (given the shape chosen for l = 3 and the wave's
   // blind rotations): their own sixteen-CTA kernel while the wave's gates fit
   // its co-resident clusters, else their eight-CTA kernel while a wave takes at
@@ -117,6 +123,12 @@ void emit_gate(uint32_t type, uint32_t w0, uint32_t w1, uint32_t w2, uint32_t ou
                std::vector<KsJob> &ks, uint32_t br_base);
 int calibrate(Engine &E, int n);
 int levelize(const arx_netlist *nl, uint32_t *wave, uint32_t *depth);
+// Moves gates between their earliest wave (wave[g] from levelize) and their
+// latest one so that each launch is filled up to its free capacity
+// (cap_of(blind rotations) = the most blind rotations at the same cost); the
+// depth is unchanged and every gate still follows its inputs.
+void balance_levels(const arx_netlist *nl, uint32_t depth, const std::function<long long(long long)> &cap_of,
+                    uint32_t *wave);
 size_t keyset_bytes(int n, int l = 3);
 int reserve_ks_scratch(DevBuf &part, DevBuf &cnt, size_t jobs, int splits);
 

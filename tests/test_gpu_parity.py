@@ -262,6 +262,28 @@ def test_graph_mode_equals_plain_mode(O, keys630, gpu630):
     assert np.array_equal(arx.client_decrypt(630, keys630.s, a), nl.plain_eval(bits))
 
 
+def test_graph_plan_balances_launch_widths(O, keys630, gpu630):
+    """Graph plans place gates within their slack: config 2's 128-wide first wave
+    and its 8- to 15-gate waves are spread so that at most one launch exceeds the
+    co-resident sixteen-CTA clusters; the depth and every ciphertext are those of
+    the plain levelization (compared with the oracle on every output)."""
+    nl = I.union([I.ripple_carry_adder(32), I.array_multiplier(8)])
+    wave, depth = arx.levelize(nl)
+    bits, ct = _encrypt_inputs(O, keys630, nl, 77)
+    out_plain = np.zeros((len(nl.outputs), 631), np.uint32)
+    arx.eval_netlist_ex(nl, ct, out_plain, mode=arx.MODE_PLAIN)
+    out = np.zeros_like(out_plain)
+    with arx.Plan(nl, mode=arx.MODE_GRAPH) as p:
+        sh = p.shapes()
+        assert p.waves == depth and sum(j for _, _, j in sh) == p.bootstraps
+        assert sum(1 for H, GT, j in sh if j > 7) <= 1, sh
+        assert max(j for _, _, j in sh) < 128
+        p.run(ct, out)
+    assert np.array_equal(out, out_plain)
+    assert np.array_equal(out, keys630.ctx.eval_netlist(nl, ct))
+    assert np.array_equal(arx.client_decrypt(630, keys630.s, out), nl.plain_eval(bits))
+
+
 def test_plan_shapes_report_every_wave(gpu630):
     nl = I.union([I.ripple_carry_adder(8), I.array_multiplier(4)])
     wave, depth = arx.levelize(nl)
@@ -463,7 +485,8 @@ def test_gadget_l2_wide_netlist_takes_the_throughput_kernel(O, keys512_l2, _load
     bits = I.random_bits(450, nl.num_inputs)
     ct = k.encrypt(O, I, bits, 451)
     out = np.zeros((len(nl.outputs), 513), np.uint32)
-    with arx.Plan(nl, keyset=ks, mode=arx.MODE_GRAPH) as p:
+    # plain mode keeps the Sec. 4.2 levels (graph plans would spread the wide wave)
+    with arx.Plan(nl, keyset=ks, mode=arx.MODE_PLAIN) as p:
         sh = p.shapes()
         assert any(H > 100 for H, GT, j in sh if j > 30) and all(H in (80, 40) for H, GT, j in sh if 0 < j <= 30)
         assert all(H == 40 for H, GT, j in sh if 16 <= j <= 30) and any(H == 80 for H, GT, j in sh if 0 < j <= 7)
