@@ -11,11 +11,12 @@
 // Per CMux: all warps compute the gadget digits of the CTA's three rows and
 // take the first two forward stages of quarter Q in prime P at once
 // (make_stage2); three pairs of forward warps (one pair per row) run the rest
-// of the quarter-Q transform of their row (fwd_quarter_pair); each warp adds
-// its half of the key products for output 1-h into CTA (1-h, Q, P)'s receive
-// slot with a bulk reduction (512 bytes) and keeps those for output h.  A pair
-// of inverse warps on two schedulers (two of the forward warps) sums the L
-// local rows and the slot (quarter Q of output h in prime P), runs the inverse
+// of the quarter-Q transform of their row (fwd_quarter_pair); each warp copies
+// its half of the key products for output 1-h into its row's receive slot at
+// CTA (1-h, Q, P) (a plain bulk copy of 512 bytes: measured faster than bulk
+// reduce-adds into one slot) and keeps those for output h.  A pair of inverse
+// warps on two schedulers (two of the forward warps) sums the L local rows and
+// the L received ones (quarter Q of output h in prime P), runs the inverse
 // quarter transform split between them (inv_quarter_pair: all stages but the
 // last two, then the quarter's share of the output twist) and posts it here and
 // at the seven CTAs (h, Q', P') (1 KiB each).  All eight CTAs of component h
@@ -59,7 +60,7 @@ struct Cfg {
   static constexpr size_t kDigBytes = (size_t)L * 256 * 4;        // [row][k] stage-2 values of quarter Q
   static constexpr size_t kOwnBytes = (size_t)L * kQuarter * 4;       // [row][quarter Q] products for output h
   static constexpr size_t kOthBytes = (size_t)2 * L * kQuarter * 4;   // [parity][row] for output 1-h
-  static constexpr size_t kSlotBytes = (size_t)2 * kQuarter * 4;      // [parity] the peer's row sum
+  static constexpr size_t kSlotBytes = (size_t)2 * L * kQuarter * 4;  // [parity][row] the peer's products
   static constexpr size_t kPostBytes = (size_t)2 * 2 * 4 * kQuarter * 4;  // [parity][prime][quarter][k]
   static constexpr size_t kScrBytes = (size_t)kCons * kQuarter * 4;
   static constexpr size_t kPairBytes = (size_t)L * kQuarter * 4;      // [row] the pass A -> B exchange
@@ -79,14 +80,14 @@ __global__ void __launch_bounds__(kThreads, 1) br_cluster16_kernel(const __grid_
   uint32_t *D = A + kN;                          // [row][k] stage-2 values (make_stage2)
   uint32_t *own = D + C::kDigBytes / 4;          // [row][256], swizzled (swp)
   uint32_t *oth = own + L * kQuarter;            // [parity][row][256], same layout
-  uint32_t *slots = oth + 2 * L * kQuarter;      // [parity][256], same layout, zero between uses
-  uint32_t *post = slots + 2 * kQuarter;         // [parity][prime][quarter][256], natural order
+  uint32_t *slots = oth + 2 * L * kQuarter;      // [parity][row][256], same layout
+  uint32_t *post = slots + 2 * L * kQuarter;     // [parity][prime][quarter][256], natural order
   uint32_t *scratch = post + 16 * kQuarter;      // [warp][256]
   uint32_t *pairbuf = scratch + kCons * kQuarter;  // [row][256]
   uint16_t *abar = reinterpret_cast<uint16_t *>(pairbuf + L * kQuarter);
   uint64_t *full = reinterpret_cast<uint64_t *>(abar + kAbarPitch);
   uint64_t *empty = full + kStages;
-  uint64_t *done1 = empty + kStages;             // [parity]: the peer's row sum in place
+  uint64_t *done1 = empty + kStages;             // [parity]: the peer's L rows in place
   uint64_t *done2 = done1 + 2;                   // [parity]: the partners' inverse quarters in place
   volatile int *abort_flag = reinterpret_cast<volatile int *>(done2 + 2);
 
@@ -108,8 +109,6 @@ __global__ void __launch_bounds__(kThreads, 1) br_cluster16_kernel(const __grid_
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  for (int k = threadIdx.x; k < 2 * kQuarter; k += kThreads) slots[k] = 0u;
-  fence_proxy_async_smem();
   cluster_sync_all();  // all sixteen CTAs initialised before any remote access
   if (threadIdx.x == 0) stamp_start(args.stamps);
 
@@ -196,7 +195,7 @@ __global__ void __launch_bounds__(kThreads, 1) br_cluster16_kernel(const __grid_
           const uint4 *Both = reinterpret_cast<const uint4 *>(ring + slot * kRowWords + (1 - h) * kN);
           const int kj = (jf & 7) * 32 + 8 * Q + (jf >> 3);
           uint32_t *oq = oth + (par * L + rr) * kQuarter;
-          // products for the peer's output first: added into its slot while the rest runs
+          // products for the peer's output first: copied into its slot of this row while the rest runs
           const uint4 b1 = Both[kj];
           reinterpret_cast<uint4 *>(oq)[s_j(jf)] =
               make_uint4(mont_mul(x[0], b1.x, pr), mont_mul(x[1], b1.y, pr), mont_mul(x[2], b1.z, pr),
@@ -204,8 +203,8 @@ __global__ void __launch_bounds__(kThreads, 1) br_cluster16_kernel(const __grid_
           fence_proxy_async_smem();
           __syncwarp();
           if (lane == 0)  // this warp's half: positions 128 fw .. 128 fw + 127, 512 bytes
-            bulk_add_s2peer(map_peer(smem_u32(slots + par * kQuarter + 128 * fw), peer), oq + 128 * fw,
-                            kQuarter * 2u, map_peer(smem_u32(done1 + par), peer));
+            bulk_s2peer(map_peer(smem_u32(slots + (par * L + rr) * kQuarter + 128 * fw), peer), oq + 128 * fw,
+                        kQuarter * 2u, map_peer(smem_u32(done1 + par), peer));
           const uint4 b0 = Bown[kj];
           reinterpret_cast<uint4 *>(own + rr * kQuarter)[s_j(jf)] =
               make_uint4(mont_mul(x[0], b0.x, pr), mont_mul(x[1], b0.y, pr), mont_mul(x[2], b0.z, pr),
@@ -220,21 +219,22 @@ __global__ void __launch_bounds__(kThreads, 1) br_cluster16_kernel(const __grid_
             mbar_expect_tx(done2 + par, kPartnerBytes);
           }
           named_bar(2, 32 * kFwd);
-          // quarter Q of output h in prime P: L local rows and the peer's sum, at 4 t + e
+          // quarter Q of output h in prime P: L local rows and the peer's L rows, at 4 t + e
+          // (the slots are read before this CTA's posts below, so before the peer can
+          // refill them two CMuxes later)
           mbar_wait(done1 + par, ph, abort_flag, args.status);
           uint32_t y[4] = {0u, 0u, 0u, 0u};
           const int ci = s_j(t);
 #pragma unroll
-          for (int r4 = 0; r4 <= L; ++r4) {
-            uint4 *sl = reinterpret_cast<uint4 *>(r4 < L ? own + r4 * kQuarter : slots + par * kQuarter);
+          for (int r4 = 0; r4 < 2 * L; ++r4) {
+            const uint4 *sl =
+                reinterpret_cast<const uint4 *>(r4 < L ? own + r4 * kQuarter : slots + (par * L + r4 - L) * kQuarter);
             const uint4 q = sl[ci];
             y[0] += q.x;
             y[1] += q.y;
             y[2] += q.z;
             y[3] += q.w;
-            if (r4 == L) sl[ci] = make_uint4(0u, 0u, 0u, 0u);  // the slot starts its next use at zero
           }
-          fence_proxy_async_smem();  // the zeroes precede the peer's next bulk additions
           inv_quarter_pair(y, scratch + kInvWarp * kQuarter, scratch + (kInvWarp + 1) * kQuarter, zp, pr, t, 3);
           // post the quarter here and at the seven CTAs (h, Q', P') (ranks rank ^ 2 j)
           uint32_t *pq = post + ((par * 2 + P) * 4 + Q) * kQuarter;
