@@ -233,22 +233,28 @@ int arx_plan_profile(int plan, const uint32_t *ct_in, float *br_ms, float *ks_ms
 int arx_set_launch_shape(int H, int GT);
 
 /* ------------------------------------------------------------ serving ---- */
-/* Continuous batching of encrypted-circuit requests from several clients.
+/* Continuous batching of encrypted-circuit requests from several clients (the
+ * paper evaluates one circuit at a time; serving is this library's addition).
  * arx_serve_start launches a scheduler thread with a wire arena of
  * wire_arena_bytes of device memory and an HBM budget (bytes of resident key
  * sets + wires of admitted requests; 0 = no budget).  Requests are admitted in
  * arrival order while their wires fit the budget and the arena; every scheduler
  * tick advances each admitted request by one wave, with the waves of all
- * requests on the same key set merged into one blind-rotation and one
- * key-switch launch (at most max_tick_bootstraps blind rotations per launch,
- * 0 = no cap; one request always runs).  Requests arriving meanwhile join at the
- * next tick.  A request's result is bit-identical to arx_eval_netlist's on the
- * same inputs, whatever else is in flight. */
+ * requests whose key sets share the LWE dimension and gadget merged into one
+ * blind-rotation and one key-switch launch, whichever client's key set each
+ * gate uses (up to 16 key sets per launch; at most max_tick_bootstraps blind
+ * rotations per launch, 0 = no cap; a larger tick takes more launches).  Ticks
+ * are pipelined: the next tick is prepared on the host while the device runs
+ * the current one.  Requests arriving meanwhile join at the next tick.  A
+ * request's result is bit-identical to arx_eval_netlist's on the same inputs,
+ * whatever else is in flight. */
 typedef struct {
   uint64_t completed, failed, gates, bootstraps, launches, ticks;
   uint64_t pending, active, peak_active, peak_bytes;
   double p50_ms, p99_ms;  /* submit-to-completion latency of completed requests */
-  double busy_s, elapsed_s;
+  double busy_s, elapsed_s; /* device time of the ticks (their events), wall time since start */
+  uint64_t shared_launches;      /* blind-rotation launches whose gates came from more than one key set */
+  uint64_t max_keys_per_launch;  /* the most key sets one launch mixed */
 } arx_serve_info;
 
 int arx_serve_start(size_t hbm_budget_bytes, size_t wire_arena_bytes, uint32_t max_tick_bootstraps);

@@ -32,7 +32,8 @@ _vp, _sz, _i, _u32, _u64 = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctype
 class ServeStats_C(ctypes.Structure):
     _fields_ = [(k, _u64) for k in ("completed", "failed", "gates", "bootstraps", "launches", "ticks", "pending",
                                     "active", "peak_active", "peak_bytes")] + \
-               [(k, ctypes.c_double) for k in ("p50_ms", "p99_ms", "busy_s", "elapsed_s")]
+               [(k, ctypes.c_double) for k in ("p50_ms", "p99_ms", "busy_s", "elapsed_s")] + \
+               [(k, _u64) for k in ("shared_launches", "max_keys_per_launch")]
 
 
 class Netlist_C(ctypes.Structure):

@@ -55,15 +55,21 @@ enum : uint32_t {
 
 constexpr unsigned int kDevTimeout = 1u;
 
-// One blind rotation: input = cst + sa * W[ia] + sb * W[ib] (LWE_n, Torus32).
+// Key sets one launch may mix (each job names its key set by an index into the
+// launch's table of key pointers).
+constexpr int kMaxLaunchKeys = 16;
+
+// One blind rotation: input = cst + sa * W[ia] + sb * W[ib] (LWE_n, Torus32),
+// with the bootstrapping key bsk[key] of the launch.
 struct BrJob {
   uint32_t ia, ib, cst;
-  int16_t sa, sb;
+  int8_t sa, sb;
+  uint16_t key;
 };
 static_assert(sizeof(BrJob) == 16, "BrJob layout");
 
 struct BrArgs {
-  const uint32_t *bsk;    // NTT-domain key: [n][6] rows of [c_out 2][prime 2][N] (per-lane order)
+  const uint32_t *bsk[kMaxLaunchKeys];  // NTT-domain keys: [n][2l] rows of [c_out 2][prime 2][N] (per-lane order)
   const uint32_t *wires;  // [*][632] LWE_n ciphertexts
   const BrJob *jobs;
   int num_jobs;
@@ -76,13 +82,14 @@ struct BrArgs {
 };
 
 // One gate output.  Bootstrapped gates key-switch br_out[j0] (+ br_out[j1] + 1/8
-// for MUX); NOT / COPY read wire ia; CONST writes a trivial sample.
+// for MUX) with the key-switching key ksk[key] of the launch; NOT / COPY read
+// wire ia; CONST writes a trivial sample.
 struct KsJob {
-  uint32_t type, j0, j1, ia, out;
+  uint32_t type, j0, j1, ia, out, key;
 };
 
 struct KsArgs {
-  const uint32_t *ksk;     // [N][8][3][632] rows for digits 1..3
+  const uint32_t *ksk[kMaxLaunchKeys];  // [N][8][3][632] rows for digits 1..3
   const uint32_t *br_out;  // [*][1028]
   const uint32_t *wires;   // [*][632]
   const KsJob *jobs;

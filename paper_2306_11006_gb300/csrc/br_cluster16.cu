@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(kThreads, 1) br_cluster16_kernel(const __grid_
               break;
             }
             mbar_expect_tx(full + slot, kRowBytes);
-            const uint32_t *row = args.bsk + ((size_t)i * 2 * L + L * h + rr) * kChunkWords;
+            const uint32_t *row = args.bsk[args.jobs[tile].key] + ((size_t)i * 2 * L + L * h + rr) * kChunkWords;
 #pragma unroll
             for (int c = 0; c < 2; ++c)  // key row layout [output][prime][N]
               bulk_g2s(ring + slot * kRowWords + c * kN, row + (c * 2 + P) * kN, kN * 4u, full + slot);

@@ -173,7 +173,7 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(kThreads, 1)
               break;
             }
             mbar_expect_tx(full + slot, kChunkBytes);
-            bulk_g2s(ring + slot * kChunkWords, args.bsk + ((size_t)i * 6 + 3 * h + rr) * kChunkWords, kChunkBytes,
+            bulk_g2s(ring + slot * kChunkWords, args.bsk[args.jobs[tile].key] + ((size_t)i * 6 + 3 * h + rr) * kChunkWords, kChunkBytes,
                      full + slot);
           }
         }

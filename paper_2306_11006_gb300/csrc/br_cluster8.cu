@@ -123,7 +123,7 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(kThreads, 1)
               break;
             }
             mbar_expect_tx(full + slot, kChunkBytes);
-            bulk_g2s(ring + slot * kChunkWords, args.bsk + ((size_t)i * 2 * L + L * h + rr) * kChunkWords,
+            bulk_g2s(ring + slot * kChunkWords, args.bsk[args.jobs[tile].key] + ((size_t)i * 2 * L + L * h + rr) * kChunkWords,
                      kChunkBytes, full + slot);
           }
         }

@@ -204,16 +204,23 @@ __device__ __forceinline__ uint32_t cta_rows(const BrArgs &args) {
   return (uint32_t)mine * (2u * L) * (uint32_t)args.n;
 }
 
-// Copy key row jc of the CTA's sequence (row jc mod 2Ln of the key: CMux i,
-// TGSW row r) into its ring slot.
-template <int kStages, int L>
-__device__ __forceinline__ void issue_row(const BrShared &S, const BrArgs &args, uint32_t jc) {
+// Copy key row jc of the CTA's sequence (row jc mod 2Ln of the key of its tile
+// jc / 2Ln: CMux i, TGSW row r) into its ring slot.  The gates of a tile share
+// one key set (the host groups them so).
+// it_hint / bsk_hint: the caller's tile iteration and that tile's key (a row of
+// another tile looks its key up).
+template <int kStages, int GT, int L>
+__device__ __forceinline__ void issue_row(const BrShared &S, const BrArgs &args, uint32_t jc, uint32_t it_hint = ~0u,
+                                          const uint32_t *bsk_hint = nullptr) {
   const uint32_t slot = jc % kStages;
+  const uint32_t per_tile = 2u * L * (uint32_t)args.n;
+  const uint32_t it = jc / per_tile;
+  const uint32_t tile = blockIdx.x + it * gridDim.x;
+  const uint32_t *bsk = it == it_hint ? bsk_hint : args.bsk[args.jobs[tile * GT].key];
   S.issued[slot] = jc + 1u;
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic reads of the slot before the copy
   mbar_expect_tx(S.full + slot, kChunkBytes);
-  bulk_g2s(S.ring + slot * kChunkWords, args.bsk + (size_t)(jc % (2u * L * (uint32_t)args.n)) * kChunkWords,
-           kChunkBytes, S.full + slot);
+  bulk_g2s(S.ring + slot * kChunkWords, bsk + (size_t)(jc % per_tile) * kChunkWords, kChunkBytes, S.full + slot);
 }
 
 // One warp (prime P, row group h) over all tiles of the launch.  The
@@ -255,6 +262,7 @@ __device__ __forceinline__ void br_consumer(const BrShared &S, const BrArgs &arg
     const int job_idx = tile * GT + g;
     const bool active = job_idx < args.num_jobs;
     const BrJob jb = args.jobs[active ? job_idx : args.num_jobs - 1];
+    const uint32_t *tile_bsk = args.bsk[args.jobs[tile * GT].key];  // the tile's gates share one key set
     const uint32_t *wa = args.wires + (size_t)jb.ia * kWireStride;
     const uint32_t *wb = args.wires + (size_t)jb.ib * kWireStride;
     const uint32_t sa = (uint32_t)(int32_t)jb.sa, sb = (uint32_t)(int32_t)jb.sb;
@@ -317,7 +325,7 @@ __device__ __forceinline__ void br_consumer(const BrShared &S, const BrArgs &arg
           if (atomicAdd(S.cnt + slot, 1u) == 2u * GT - 1u) {
             __threadfence_block();
             S.cnt[slot] = 0u;
-            if (jc + kStages < rows) issue_row<kStages, L>(S, args, jc + kStages);
+            if (jc + kStages < rows) issue_row<kStages, GT, L>(S, args, jc + kStages, it, tile_bsk);
           }
         }
       }
@@ -423,7 +431,7 @@ __global__ void __launch_bounds__(2 * H * GT * 32, 1) br_kernel(const __grid_con
   if (args.num_jobs <= 0) return;
   if (threadIdx.x == 0) {  // the first kStages rows; later ones are issued by the warps
     const uint32_t rows = cta_rows<GT, L>(args);
-    for (uint32_t jc = 0; jc < (uint32_t)kStages && jc < rows; ++jc) issue_row<kStages, L>(S, args, jc);
+    for (uint32_t jc = 0; jc < (uint32_t)kStages && jc < rows; ++jc) issue_row<kStages, GT, L>(S, args, jc);
   }
   const int g = warp / (2 * H), role = warp % (2 * H);
   br_consumer<H, GT, L>(S, args, g, role >> 1, role & 1, lane);

@@ -133,7 +133,7 @@ int read_status(Engine &E, cudaStream_t st) {
 // --------------------------------------------------------------------------
 // gate linear parts (Fig. 2 top box; constants as in the design notes)
 // --------------------------------------------------------------------------
-bool gate_linear(uint32_t type, int16_t *sa, int16_t *sb, uint32_t *cst) {
+bool gate_linear(uint32_t type, int8_t *sa, int8_t *sb, uint32_t *cst) {
   const uint32_t e = ARX_MU, q = 2u * ARX_MU;
   switch (type) {
     case ARX_AND: *sa = 1; *sb = 1; *cst = 0u - e; return true;
@@ -310,7 +310,7 @@ int calibrate(Engine &E, int n) {
   for (BrShape s : kShapes) {
     if (!E.policy.occupancy(s)) continue;
     BrArgs args{};
-    args.bsk = bsk.as<uint32_t>();
+    args.bsk[0] = bsk.as<uint32_t>();
     args.wires = wires.as<uint32_t>();
     args.jobs = jobs.as<BrJob>();
     args.num_jobs = is_cluster_shape(s) ? E.policy.occupancy(s) : E.sms * s.GT * E.policy.occupancy(s);
@@ -582,7 +582,7 @@ int plan_launch_levels(Engine &E, Plan &P, cudaStream_t st) {
   for (const Level &L : P.levels) {
     if (L.br_cnt) {
       BrArgs a{};
-      a.bsk = ks.bsk;
+      a.bsk[0] = ks.bsk;
       a.wires = P.wires.as<uint32_t>();
       a.jobs = P.brjobs.as<BrJob>() + L.br_off;
       a.num_jobs = L.br_cnt;
@@ -594,7 +594,7 @@ int plan_launch_levels(Engine &E, Plan &P, cudaStream_t st) {
       CK(launch_br(a, L.shape, L.grid, st));
     }
     KsArgs k{};
-    k.ksk = ks.ksk;
+    k.ksk[0] = ks.ksk;
     k.br_out = P.brout.as<uint32_t>();
     k.wires = P.wires.as<uint32_t>();
     k.jobs = P.ksjobs.as<KsJob>() + L.ks_off;
@@ -707,7 +707,7 @@ int bootstrap_gates(Engine &E, const uint8_t *types, const uint32_t *a, const ui
   CK(cudaMemcpyAsync(W.ksjobs.p, ksj.data(), ksj.size() * sizeof(KsJob), cudaMemcpyHostToDevice, st));
   if (!br.empty()) {
     BrArgs args{};
-    args.bsk = ks->bsk;
+    args.bsk[0] = ks->bsk;
     args.wires = W.wires.as<uint32_t>();
     args.jobs = W.brjobs.as<BrJob>();
     args.num_jobs = (int)br.size();
@@ -722,7 +722,7 @@ int bootstrap_gates(Engine &E, const uint8_t *types, const uint32_t *a, const ui
   const bool dev_out = is_device_ptr(out);
   if (!dev_out) CK(W.out.reserve(count * row * 4));
   KsArgs k{};
-  k.ksk = ks->ksk;
+  k.ksk[0] = ks->ksk;
   k.br_out = W.brout.as<uint32_t>();
   k.wires = W.wires.as<uint32_t>();
   k.jobs = W.ksjobs.as<KsJob>();
@@ -1043,7 +1043,7 @@ extern "C" int arx_plan_profile(int plan, const uint32_t *ct_in, float *br_ms, f
     CK(cudaEventRecord(ev[4 * l], st));
     if (L.br_cnt) {
       BrArgs a{};
-      a.bsk = ks->bsk;
+      a.bsk[0] = ks->bsk;
       a.wires = P.wires.as<uint32_t>();
       a.jobs = P.brjobs.as<BrJob>() + L.br_off;
       a.num_jobs = L.br_cnt;
@@ -1058,7 +1058,7 @@ extern "C" int arx_plan_profile(int plan, const uint32_t *ct_in, float *br_ms, f
     CK(cudaEventRecord(ev[4 * l + 1], st));
     CK(cudaEventRecord(ev[4 * l + 2], st));
     KsArgs k{};
-    k.ksk = ks->ksk;
+    k.ksk[0] = ks->ksk;
     k.br_out = P.brout.as<uint32_t>();
     k.wires = P.wires.as<uint32_t>();
     k.jobs = P.ksjobs.as<KsJob>() + L.ks_off;

@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(kKsThreads) ks_kernel(const __grid_constant__ 
     if (n == 4 * t) acc.x = b; else if (n == 4 * t + 1) acc.y = b; else if (n == 4 * t + 2) acc.z = b; else acc.w = b;
   }
   const bool live = t < kKsVec;
-  const uint4 *__restrict__ ksk = reinterpret_cast<const uint4 *>(args.ksk);
+  const uint4 *__restrict__ ksk = reinterpret_cast<const uint4 *>(args.ksk[jb.key]);
 #pragma unroll 1
   for (int i = i0; i < i1; i += 4) {  // 4 positions x 8 digits: 32 key rows in flight (kN / S >= 16)
     uint4 r[32];

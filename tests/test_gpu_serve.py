@@ -122,3 +122,73 @@ def test_bad_requests_rejected_without_disturbing_others(O, clients):
         assert e.value.code == -2
         out = srv.wait(good)
     assert np.array_equal(arx.client_decrypt(630, keys.s, out), nl.plain_eval(b))
+
+
+class _Client:
+    def __init__(self, O, seed, n):
+        self.n = n
+        kr = I.key_randomness(seed, n)
+        self.s = kr.s
+        self.bsk, self.ksk = O.keygen(kr)
+        self.ctx = O.Context(n, self.bsk, self.ksk)
+
+    def encrypt(self, O, I_, bits, seed):
+        m, e = I_.encryption_randomness(seed, len(bits), self.n)
+        return O.encrypt(self.n, self.s, m, e, np.asarray(bits, np.uint8))
+
+
+@pytest.fixture(scope="module")
+def second630(O, clients):
+    """A second client with its own n = 630 keys (same parameter set as client a)."""
+    keys = _Client(O, 21, 630)
+    ks = arx.load_keys(keys.bsk, keys.ksk, 630)
+    yield keys, ks
+    arx.unload_keys(ks)
+
+
+def test_clients_on_different_key_sets_share_launches(O, clients, second630):
+    """Two clients with their own key sets of the same parameter set: their
+    waves run in the same launches (one blind-rotation and one key-switch launch
+    per tick), and each result equals the oracle's and the one computed alone."""
+    (ka, sa), (kb, sb) = clients["a"], second630
+    nl = I.union([I.ripple_carry_adder(6), I.comparator(4)])
+    wave, depth = arx.levelize(nl)
+    reqs = []
+    for k, (keys, ks) in enumerate(((ka, sa), (kb, sb))):
+        bits = I.random_bits(6000 + k, nl.num_inputs)
+        reqs.append((keys, ks, bits, keys.encrypt(O, I, bits, 6100 + k)))
+    with arx.Server(arena_bytes=64 << 20) as srv:
+        ids = [srv.submit(nl, ct, keyset=ks) for keys, ks, bits, ct in reqs]
+        outs = [srv.wait(i) for i in ids]
+        st = srv.stats()
+    assert st["completed"] == 2 and st["failed"] == 0
+    # merged: at most one tick of offset; apart: two launches per wave per client
+    assert st["launches"] <= 2 * depth + 2, st
+    assert st["shared_launches"] >= 1 and st["max_keys_per_launch"] == 2, st
+    for (keys, ks, bits, ct), out in zip(reqs, outs):
+        assert np.array_equal(out, keys.ctx.eval_netlist(nl, ct))
+        assert np.array_equal(arx.client_decrypt(630, keys.s, out), nl.plain_eval(bits))
+
+
+def test_throughput_tiles_never_mix_key_sets(O, clients, second630):
+    """Wide waves from two key sets in one launch of the throughput kernel (several
+    gates per CTA tile; 301 gates per client, so that each key set's group is
+    padded to whole tiles): every sampled ciphertext equals the oracle's."""
+    (ka, sa), (kb, sb) = clients["a"], second630
+    g = 301
+    types = I.random_gate_types(61, g)
+    nl = I.Netlist(2 * g, types, np.arange(g, dtype=np.uint32), np.arange(g, 2 * g, dtype=np.uint32),
+                   np.zeros(g, np.uint32), np.arange(2 * g, 3 * g, dtype=np.uint32), "gates301")
+    reqs = []
+    for k, (keys, ks) in enumerate(((ka, sa), (kb, sb))):
+        bits = I.random_bits(6200 + k, nl.num_inputs)
+        reqs.append((keys, ks, bits, keys.encrypt(O, I, bits, 6300 + k)))
+    with arx.Server(arena_bytes=64 << 20) as srv:
+        ids = [srv.submit(nl, ct, keyset=ks) for keys, ks, bits, ct in reqs]
+        outs = [srv.wait(i) for i in ids]
+    rng = np.random.default_rng(5)
+    for (keys, ks, bits, ct), out in zip(reqs, outs):
+        assert np.array_equal(arx.client_decrypt(630, keys.s, out), nl.plain_eval(bits))
+        pick = np.sort(rng.choice(g, 12, replace=False))
+        want = keys.ctx.gates(types[pick], ct[pick], ct[g + pick])
+        assert np.array_equal(out[pick], want)
