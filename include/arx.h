@@ -97,6 +97,10 @@ int arx_load_keys_ex(const uint32_t *bsk, const uint32_t *ksk, int lwe_n, void *
  * ARX_EINVAL for any other gadget. */
 int arx_load_keys_gadget(const uint32_t *bsk, const uint32_t *ksk, int lwe_n, int l, int bg_bits, void *stream);
 
+/* LWE dimension and gadget length of a loaded key set (-1 = the default one);
+ * either pointer may be NULL.  ARX_ENOKEYS for an unknown id. */
+int arx_keyset_dims(int keyset, int *lwe_n, int *l);
+
 /* Free a key set.  ARX_EBUSY while a plan references it. */
 int arx_unload_keys(int keyset);
 

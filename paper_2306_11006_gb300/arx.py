@@ -47,6 +47,7 @@ SIGNATURES = {
     "arx_load_keys_ex": (_i, [_vp, _vp, _i, _vp]),
     "arx_load_keys_gadget": (_i, [_vp, _vp, _i, _i, _i, _vp]),
     "arx_unload_keys": (_i, [_i]),
+    "arx_keyset_dims": (_i, [_i, _vp, _vp]),
     "arx_use_keys": (_i, [_i]),
     "arx_keyset_bytes": (_sz, [_i]),
     "arx_resident_bytes": (_sz, []),
@@ -150,6 +151,13 @@ def load_keys(bsk, ksk, lwe_n: int = LWE_N, stream=None, l: int = 3) -> int:
         return _check(lib().arx_load_keys_ex(_ptr(bsk), _ptr(ksk), lwe_n, _stream(stream)))
     return _check(lib().arx_load_keys_gadget(_ptr(bsk), _ptr(ksk), lwe_n, l, GADGET_BITS.get(l, 0),
                                              _stream(stream)))
+
+
+def keyset_dims(keyset: int = -1) -> tuple:
+    """(LWE dimension n, gadget length l) of a loaded key set."""
+    n, l = ctypes.c_int(0), ctypes.c_int(0)
+    _check(lib().arx_keyset_dims(keyset, ctypes.addressof(n), ctypes.addressof(l)))
+    return n.value, l.value
 
 
 def unload_keys(keyset: int) -> None:
@@ -277,10 +285,34 @@ class Plan:
 KS_NOALLOC_MAX = 1024
 
 
+def _check_noalloc_args(lwe_N, ct_out, count, n):
+    """The shapes the C-ABI cannot see: raises ArxError(ARX_EINVAL) before any
+    pointer reaches the library."""
+    def bad(msg):
+        raise ArxError(-1, msg)
+
+    for name, t in (("lwe_N", lwe_N), ("ct_out", ct_out)):
+        if not hasattr(t, "is_cuda") or not t.is_cuda:
+            bad(f"{name} must be a CUDA tensor")
+        if str(t.dtype) not in ("torch.int32", "torch.uint32"):
+            bad(f"{name} must hold 32-bit words, not {t.dtype}")
+        if t.dim() != 2 or not t.is_contiguous():
+            bad(f"{name} must be a contiguous 2-D tensor")
+    if lwe_N.shape[1] != N + 1:
+        bad(f"lwe_N rows have {lwe_N.shape[1]} words, not N + 1 = {N + 1}")
+    if ct_out.shape[1] != n + 1:
+        bad(f"ct_out rows have {ct_out.shape[1]} words, not n + 1 = {n + 1} of the key set")
+    if count < 0 or count > lwe_N.shape[0] or count > ct_out.shape[0]:
+        bad(f"count {count} exceeds lwe_N ({lwe_N.shape[0]} rows) or ct_out ({ct_out.shape[0]} rows)")
+
+
 def keyswitch_noalloc(lwe_N, ct_out, count=None, keyset: int = -1, stream=None) -> None:
     """Key switch of LWE_N samples into LWE_n ciphertexts (device tensors) with no
-    device allocation inside the call (see include/arx.h)."""
+    device allocation inside the call (see include/arx.h).  The tensors' device,
+    word size, row widths and count are checked here first."""
     count = len(lwe_N) if count is None else count
+    n, _ = keyset_dims(keyset)
+    _check_noalloc_args(lwe_N, ct_out, count, n)
     _check(lib().arx_keyswitch_noalloc(_ptr(lwe_N), _ptr(ct_out), count, keyset, _stream(stream)))
 
 

@@ -6,7 +6,9 @@
 // here each product is carried modulo two 27-bit primes (CRT), so every modular
 // multiply is a native 32-bit IMAD / IMAD.HI sequence:
 //   q0 = 134215681, q1 = 134203393, both = 1 (mod 2048), q0 q1 > 2^53,
-// while the exact products are bounded by 6 * 1024 * 64 * 2^31 < 2^50.
+// while the exact products are bounded by 6 * 1024 * 64 * 2^31 < 2^50 for the
+// gadget l = 3 (Bg = 2^7) and by 4 * 1024 * 512 * 2^31 = 2^52 for l = 2
+// (Bg = 2^10): both below q0 q1 / 2 > 2^53.
 //
 // Warp-per-transform layout: a 1024-point transform is held by one warp, 32
 // values per lane.  Forward (negacyclic Cooley-Tukey with merged twist, natural

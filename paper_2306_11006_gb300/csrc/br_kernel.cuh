@@ -110,11 +110,16 @@ __device__ __forceinline__ uint32_t modswitch(uint32_t x) { return (x + (1u << 2
 
 // (x0 mod q0, x1 mod q1), each in [0, 2q) -> the centred integer V, mod 2^32.
 // Garner: X = x0 + q0 k, k = (x1 - x0) q0^-1 mod q1 fully reduced (d stays in
-// (0, 2^32) for these input ranges).  |V| < 2^50, so the coefficient K of V's
-// representative in [0, q0 q1) is below 2^23 (V >= 0) or above q1 - 2^23
-// (V < 0): V is negative exactly when k >= q1 / 2, and then X - q0 q1 = V.  An
-// x0 one q0 above its residue gives k = K - 1; for K = 0 (0 <= V < q0) that
-// wraps to q1 - 1, X = V + q0 q1, and the same rule returns V.
+// (0, 2^32) for these input ranges).  |V| < 2^50 for the gadget l = 3 and
+// |V| <= 2^52 for l = 2, so the coefficient K of V's representative in
+// [0, q0 q1) is below 2^23 (l = 3) or 2^25 + 2^12 (l = 2; 2^52 / q0 is just
+// above 2^25) when V >= 0, and above q1 minus those when V < 0; q1 / 2 > 2^26
+// lies between (a margin of 8x for l = 3, 2x for l = 2): V is negative exactly
+// when k >= q1 / 2, and
+// then X - q0 q1 = V.  An x0 one q0 above its residue gives k = K - 1; for
+// K = 0 (0 <= V < q0) that wraps to q1 - 1, X = V + q0 q1, and the same rule
+// returns V.  (The worst cases of both gadgets are checked on the CPU in
+// tests/test_crt_bounds.py.)
 __device__ __forceinline__ uint32_t crt_torus(uint32_t x0, uint32_t x1) {
   const uint32_t d = x1 + 3u * kQ1 - x0;
   const uint32_t k = csub(shoup_mul(kQ0InvQ1, kQ0InvQ1Shoup, d, kQ1), kQ1);

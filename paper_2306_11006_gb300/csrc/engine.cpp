@@ -859,6 +859,16 @@ extern "C" int arx_load_keys_gadget(const uint32_t *bsk, const uint32_t *ksk, in
   return load_keys(E, bsk, ksk, lwe_n, l, (cudaStream_t)stream);
 }
 
+extern "C" int arx_keyset_dims(int keyset, int *lwe_n, int *l) {
+  API_BEGIN
+  Keyset *ks = nullptr;
+  int rc = resolve_keyset(E, keyset, &ks);
+  if (rc) return rc;
+  if (lwe_n) *lwe_n = ks->n;
+  if (l) *l = ks->l;
+  return ARX_OK;
+}
+
 extern "C" int arx_unload_keys(int keyset) {
   API_BEGIN
   return unload_keys(E, keyset);

@@ -150,3 +150,35 @@ def test_client_encrypt_decrypt_match_oracle(O):
 def test_keyset_bytes():
     assert arx.keyset_bytes(630) == 630 * 6 * 16384 + 1024 * 8 * 3 * 632 * 4
     assert arx.keyset_bytes(0) == 0
+
+
+class _FakeTensor:
+    """Stands in for a torch tensor's metadata (no device memory is touched)."""
+
+    def __init__(self, shape, dtype="torch.int32", is_cuda=True, contiguous=True):
+        self.shape, self.dtype, self.is_cuda, self._c = tuple(shape), dtype, is_cuda, contiguous
+
+    def dim(self):
+        return len(self.shape)
+
+    def is_contiguous(self):
+        return self._c
+
+
+@pytest.mark.parametrize("case", ["host", "dtype", "noncontig", "rows_N", "rows_n", "count_in", "count_out",
+                                  "negative"])
+def test_keyswitch_noalloc_argument_checks(case):
+    n = 630
+    good_in, good_out = _FakeTensor((8, 1025)), _FakeTensor((8, n + 1))
+    args = {"host": (_FakeTensor((8, 1025), is_cuda=False), good_out, 8),
+            "dtype": (good_in, _FakeTensor((8, n + 1), dtype="torch.int64"), 8),
+            "noncontig": (_FakeTensor((8, 1025), contiguous=False), good_out, 8),
+            "rows_N": (_FakeTensor((8, 1024)), good_out, 8),
+            "rows_n": (good_in, _FakeTensor((8, 513)), 8),
+            "count_in": (_FakeTensor((4, 1025)), good_out, 8),
+            "count_out": (good_in, _FakeTensor((4, n + 1)), 8),
+            "negative": (good_in, good_out, -1)}[case]
+    with pytest.raises(arx.ArxError) as e:
+        arx._check_noalloc_args(*args, n)
+    assert e.value.code == -1
+    arx._check_noalloc_args(good_in, good_out, 8, n)  # the valid form passes
