@@ -285,12 +285,14 @@ int ShapePolicy::grid(BrShape s, int jobs) {
   return std::max(1, std::min(tiles, cap));
 }
 
-// Autotuner: time one full wave of every shape once per (device, n) with a short
-// synthetic blind rotation (timing is data-independent), then pick the shape
-// minimising waves x time-per-wave for each launch width.
+// Autotuner: time one full wave of every shape once per (device, n) with short
+// synthetic blind rotations (timing is data-independent) of two lengths, and
+// take the time per CMux as the slope between them (the launch's fixed start-up
+// -- ring fill, twiddle loads -- drops out, as it does in a 630-CMux wave); then
+// pick the shape minimising waves x time-per-wave for each launch width.
 int calibrate(Engine &E, int n) {
   if (E.policy.tuned_n == n) return ARX_OK;
-  const int ncal = std::min(n, 16);
+  const int ncal = std::min(n, 40), nshort = std::min(ncal, 8);
   int max_jobs = 0;
   for (BrShape s : kShapes) max_jobs = std::max(max_jobs, is_cluster_shape(s) ? E.policy.occupancy(s) : E.sms * s.GT * std::max(1, E.policy.occupancy(s)));
   DevBuf bsk, wires, jobs, out;
@@ -321,20 +323,24 @@ int calibrate(Engine &E, int n) {
     args.tc = E.tc;
     args.stamps = stamps.as<unsigned long long>();
     const int grid = E.policy.grid(s, args.num_jobs);
-    double best = 1e30;
-    for (int rep = 0; rep < 3; ++rep) {
-      CK(cudaMemsetAsync(stamps.p, 0xFF, sizeof(unsigned long long), E.stream));
-      CK(cudaMemsetAsync(stamps.as<unsigned long long>() + 1, 0, sizeof(unsigned long long), E.stream));
-      CK(launch_br(args, s, grid, E.stream));
-      unsigned long long t[2] = {0, 0};
-      CK(cudaMemcpyAsync(t, stamps.p, sizeof(t), cudaMemcpyDeviceToHost, E.stream));
-      CK(cudaStreamSynchronize(E.stream));
-      const double ms = t[1] > t[0] ? (t[1] - t[0]) * 1e-6 : 1e30;
-      if (rep) best = std::min(best, ms);
+    double best[2] = {1e30, 1e30};  // shortest time over the repetitions, for nshort and ncal CMux
+    for (int len = 0; len < 2; ++len) {
+      args.n = len ? ncal : nshort;
+      for (int rep = 0; rep < 4; ++rep) {
+        CK(cudaMemsetAsync(stamps.p, 0xFF, sizeof(unsigned long long), E.stream));
+        CK(cudaMemsetAsync(stamps.as<unsigned long long>() + 1, 0, sizeof(unsigned long long), E.stream));
+        CK(launch_br(args, s, grid, E.stream));
+        unsigned long long t[2] = {0, 0};
+        CK(cudaMemcpyAsync(t, stamps.p, sizeof(t), cudaMemcpyDeviceToHost, E.stream));
+        CK(cudaStreamSynchronize(E.stream));
+        const double ms = t[1] > t[0] ? (t[1] - t[0]) * 1e-6 : 1e30;
+        if (rep) best[len] = std::min(best[len], ms);
+      }
     }
     TuneEntry t;
     t.shape = s;
-    t.wave_ms_per_cmux = best / ncal;
+    const double slope = ncal > nshort ? (best[1] - best[0]) / (ncal - nshort) : 0.0;
+    t.wave_ms_per_cmux = slope > 0.0 ? slope : best[1] / ncal;
     t.gates_per_wave = args.num_jobs;
     E.policy.tune.push_back(t);
   }

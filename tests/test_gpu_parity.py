@@ -132,6 +132,58 @@ def test_device_pointers_and_streams(O, keys630, gpu630, torch_cuda):
     assert np.array_equal(dout.cpu().numpy().view(np.uint32), want)
 
 
+def _tie_ciphertexts(n, count, seed):
+    """Mask and body words on the rounding ties of the mod switch (k 2^21 + 2^20,
+    which rounds up), at 2^31, 2^32 - 1 and 0, mixed with random words: not
+    encryptions of anything, but every gate is a fixed integer function of its
+    input words, so the GPU must reproduce the oracle on them bit for bit."""
+    rng = np.random.default_rng(seed)
+    ties = (rng.integers(0, 2048, (count, n + 1), dtype=np.uint64) << 21) + (1 << 20)
+    special = np.array([1 << 31, (1 << 32) - 1, 0, 1 << 20, (1 << 21) - 1, 1 << 21], np.uint64)
+    pick = rng.integers(0, 4, (count, n + 1))
+    out = np.where(pick == 0, ties, np.where(pick == 1, special[rng.integers(0, len(special), (count, n + 1))],
+                                            rng.integers(0, 1 << 32, (count, n + 1), dtype=np.uint64)))
+    out[:, :: 7] = ties[:, :: 7]
+    return out.astype(np.uint32)
+
+
+def test_rounding_ties_bit_exact(O, keys630, gpu630):
+    """Linear combinations landing exactly on the mod-switch half points (and the
+    words 0, 2^31, 2^32 - 1): with b = 0 the combination of AND / OR / NAND /
+    NOR is +-a plus the constant, so ties in a give ties in the combination."""
+    n, g = 630, 48
+    types = np.array([[I.AND, I.OR, I.NAND, I.NOR, I.XOR, I.XNOR][k % 6] for k in range(g)], np.uint8)
+    ca = _tie_ciphertexts(n, g, 71)
+    cb = np.zeros_like(ca)
+    cb[g // 2:] = _tie_ciphertexts(n, g - g // 2, 72)  # both operands on ties for the second half
+    for body in (0, 1 << 20, (1 << 21) + (1 << 20), (1 << 32) - (1 << 29) + (1 << 20)):
+        ca[: g // 4, n] = body
+    want = keys630.ctx.gates(types, ca, cb)
+    out = np.zeros_like(ca)
+    arx.bootstrap_gates_ex(types, ca, cb, None, out, keyset=gpu630)
+    assert np.array_equal(out, want)
+
+
+def test_aliased_buffers(O, keys630, gpu630, torch_cuda):
+    """ct_out may be ct_a (the inputs reach the device before any output is
+    written), and ct_a may be ct_b."""
+    torch = torch_cuda
+    types = I.random_gate_types(80, 20)
+    xs, ys, zs, ca, cb, cc = _inputs(O, I, keys630, types, 81)
+    want_ab = keys630.ctx.gates(types, ca, cb)
+    want_aa = keys630.ctx.gates(types, ca, ca)
+    da, db = torch.from_numpy(ca.view(np.int32)).cuda(), torch.from_numpy(cb.view(np.int32)).cuda()
+    arx.bootstrap_gates_ex(types, da, db, None, da, keyset=gpu630)  # out == a
+    assert np.array_equal(da.cpu().numpy().view(np.uint32), want_ab)
+    da2 = torch.from_numpy(ca.view(np.int32)).cuda()
+    out = torch.zeros_like(da2)
+    arx.bootstrap_gates_ex(types, da2, da2, None, out, keyset=gpu630)  # a == b
+    assert np.array_equal(out.cpu().numpy().view(np.uint32), want_aa)
+    h = ca.copy()
+    arx.bootstrap_gates_ex(types, h, cb, None, h, keyset=gpu630)  # host buffers, out == a
+    assert np.array_equal(h, want_ab)
+
+
 def test_empty_and_single_gate(O, keys630, gpu630):
     arx.bootstrap_gates(np.zeros(0, np.uint8), np.zeros((0, 631), np.uint32), np.zeros((0, 631), np.uint32),
                         np.zeros((0, 631), np.uint32))
