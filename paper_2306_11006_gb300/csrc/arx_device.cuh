@@ -95,18 +95,21 @@ __device__ __forceinline__ void ct_bfly(uint32_t &x, uint32_t &y, uint2 z, const
 __device__ __forceinline__ int swz(int r, int c) { return r * 32 + ((((c >> 2) ^ (r & 7))) << 2) + (c & 3); }
 
 // ---- warp transforms ----------------------------------------------------
-// Forward.  kDigits: x[e] holds raw gadget digit bytes u = d + 64 in [0, 128) of
-// a[lane + 32 e]; the -64 offsets ride on the first stage's constants.
-// Otherwise x[e] < q.  Output: x[e] = A[32 lane + e] < 22 q.
+// Forward.  kDigits: x[e] holds raw gadget digits u = d + Bg/2 in [0, Bg) of
+// a[lane + 32 e]; the -Bg/2 offsets ride on the first stage's constants, and
+// the first stage's products zeta[1] u come from dtab[u] (zeta[1] u mod q,
+// fully reduced, built once per CTA: a shared-memory load instead of a Shoup
+// product).  Otherwise x[e] < q.  Output: x[e] = A[32 lane + e] < 22 q.
 template <bool kDigits>
 __device__ __forceinline__ void ntt_fwd(uint32_t (&x)[32], uint32_t *xbuf, const uint2 *tw1,
-                                        const uint2 *__restrict__ tw2, const PrimeRT &pr, int lane) {
+                                        const uint2 *__restrict__ tw2, const PrimeRT &pr, int lane,
+                                        const uint32_t *dtab = nullptr) {
   {
     const uint2 z = tw1[1];
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
       if (kDigits) {
-        const uint32_t t = shoup_mul(z.x, z.y, x[e + 16], pr.q);
+        const uint32_t t = dtab[x[e + 16]];
         const uint32_t u = x[e];
         x[e] = u + t + pr.dc;
         x[e + 16] = u - t + pr.q2 + pr.dd;

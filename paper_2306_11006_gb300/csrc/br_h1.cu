@@ -25,10 +25,10 @@ cudaError_t launch_br_h1(const BrArgs &args, int GT, int L, int grid, cudaStream
 size_t br_smem_h1(int GT, int L) {
   if (L == 2) {
     switch (GT) {
-      case 1: return br::br_smem_bytes<1, 1>();
-      case 2: return br::br_smem_bytes<1, 2>();
-      case 4: return br::br_smem_bytes<1, 4>();
-      case 6: return br::br_smem_bytes<1, 6>();
+      case 1: return br::br_smem_bytes<1, 1, 2>();
+      case 2: return br::br_smem_bytes<1, 2, 2>();
+      case 4: return br::br_smem_bytes<1, 4, 2>();
+      case 6: return br::br_smem_bytes<1, 6, 2>();
       default: return 0;
     }
   }

@@ -21,8 +21,8 @@ cudaError_t launch_br_h2(const BrArgs &args, int GT, int L, int grid, cudaStream
 size_t br_smem_h2(int GT, int L) {
   if (L == 2) {
     switch (GT) {
-      case 1: return br::br_smem_bytes<2, 1>();
-      case 3: return br::br_smem_bytes<2, 3>();
+      case 1: return br::br_smem_bytes<2, 1, 2>();
+      case 3: return br::br_smem_bytes<2, 3, 2>();
       default: return 0;
     }
   }

@@ -16,7 +16,7 @@ cudaError_t launch_br_h4(const BrArgs &args, int GT, int L, int grid, cudaStream
 size_t br_smem_h4(int GT, int L) {
   if (L == 2) {
     switch (GT) {
-      case 1: return br::br_smem_bytes<4, 1>();
+      case 1: return br::br_smem_bytes<4, 1, 2>();
       default: return 0;
     }
   }

@@ -152,6 +152,7 @@ __device__ __forceinline__ void make_digits(uint32_t *dig, const uint32_t *A, ui
 
 struct BrShared {
   uint32_t *ring;     // kStages x kChunkWords
+  uint32_t *dtab;     // [prime][Bg]: zeta[1] u mod q for every digit value u (first forward stage)
   uint32_t *acc;      // GT x [2][N]
   uint32_t *dig;      // GT x [2][N] packed gadget digits
   uint32_t *scratch;  // consumer warps x kScratch
@@ -168,29 +169,35 @@ constexpr size_t kSmemLimit = 227 * 1024;  // opt-in shared memory per CTA
 template <int H>
 __host__ __device__ constexpr int scratch_words() { return (H == 1 ? 1 : 2) * kXpose; }
 
-template <int H, int GT>
+// Digit values of the gadget: Bg (7-bit digits for L = 3, 10-bit for L = 2).
+template <int L>
+__host__ __device__ constexpr int digit_values() { return L == 3 ? 128 : 1024; }
+
+template <int H, int GT, int L = 3>
 constexpr size_t br_fixed_bytes() {
-  return (size_t)GT * 4 * kN * 4 + (size_t)2 * H * GT * scratch_words<H>() * 4 + (size_t)GT * kAbarPitch * 2 + 2 * 8 * 8 + 16;
+  return (size_t)GT * 4 * kN * 4 + (size_t)2 * H * GT * scratch_words<H>() * 4 + (size_t)GT * kAbarPitch * 2 +
+         (size_t)2 * digit_values<L>() * 4 + 2 * 8 * 8 + 16;
 }
 
 // Ring depth: as many key rows in flight as shared memory allows, 4..8.
-template <int H, int GT>
+template <int H, int GT, int L = 3>
 __host__ __device__ constexpr int br_stages() {
-  return (kSmemLimit - br_fixed_bytes<H, GT>()) / kChunkBytes >= 8 ? 8
-         : (int)((kSmemLimit - br_fixed_bytes<H, GT>()) / kChunkBytes);
+  return (kSmemLimit - br_fixed_bytes<H, GT, L>()) / kChunkBytes >= 8 ? 8
+         : (int)((kSmemLimit - br_fixed_bytes<H, GT, L>()) / kChunkBytes);
 }
 
-template <int H, int GT>
+template <int H, int GT, int L = 3>
 constexpr size_t br_smem_bytes() {
-  return (size_t)br_stages<H, GT>() * kChunkBytes + br_fixed_bytes<H, GT>();
+  return (size_t)br_stages<H, GT, L>() * kChunkBytes + br_fixed_bytes<H, GT, L>();
 }
 
-template <int H, int GT>
+template <int H, int GT, int L = 3>
 __device__ __forceinline__ BrShared br_carve(uint8_t *smem) {
-  constexpr int kStages = br_stages<H, GT>();
+  constexpr int kStages = br_stages<H, GT, L>();
   BrShared s;
   s.ring = reinterpret_cast<uint32_t *>(smem);
-  s.acc = s.ring + kStages * kChunkWords;
+  s.dtab = s.ring + kStages * kChunkWords;
+  s.acc = s.dtab + 2 * digit_values<L>();
   s.dig = s.acc + GT * 2 * kN;
   s.scratch = s.dig + GT * 2 * kN;
   s.abar = reinterpret_cast<uint16_t *>(s.scratch + 2 * H * GT * scratch_words<H>());
@@ -238,7 +245,7 @@ __device__ __forceinline__ void br_consumer(const BrShared &S, const BrArgs &arg
   constexpr int kRpg = kRows / H;
   constexpr int kScr = scratch_words<H>();
   constexpr int kGateThreads = 64 * H;
-  constexpr int kStages = br_stages<H, GT>();
+  constexpr int kStages = br_stages<H, GT, L>();
   const int n = args.n;
   const int bar_id = 1 + g;
   const int role = h * 2 + P;
@@ -304,7 +311,7 @@ __device__ __forceinline__ void br_consumer(const BrShared &S, const BrArgs &arg
 #pragma unroll
           for (int e = 0; e < 32; ++e) x[e] = (dc[lane + 32 * e] >> sh) & 0xFFFFu;
         }
-        ntt_fwd<true>(x, myscr, tw1f, tw2f, pr, lane);
+        ntt_fwd<true>(x, myscr, tw1f, tw2f, pr, lane, S.dtab + P * digit_values<L>());
         // MAC with the NTT-domain key row staged in the ring.
         const uint32_t jc = (it * (uint32_t)n + (uint32_t)i) * (uint32_t)kRows + (uint32_t)r;
         const uint32_t slot = jc % kStages;
@@ -418,9 +425,9 @@ __device__ __forceinline__ void br_consumer(const BrShared &S, const BrArgs &arg
 template <int H, int GT, int L>
 __global__ void __launch_bounds__(2 * H * GT * 32, 1) br_kernel(const __grid_constant__ BrArgs args) {
   extern __shared__ __align__(128) uint8_t smem[];
-  BrShared S = br_carve<H, GT>(smem);
+  BrShared S = br_carve<H, GT, L>(smem);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  constexpr int kStages = br_stages<H, GT>();
+  constexpr int kStages = br_stages<H, GT, L>();
   static_assert(kStages >= 4 && kStages <= 8, "ring depth");
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -430,6 +437,12 @@ __global__ void __launch_bounds__(2 * H * GT * 32, 1) br_kernel(const __grid_con
     }
     *S.abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  for (int k = threadIdx.x; k < 2 * digit_values<L>(); k += blockDim.x) {  // zeta[1] u mod q per prime
+    const int P = k / digit_values<L>();
+    const uint32_t q = P ? kQ1 : kQ0;
+    const uint2 z = args.tc.fwd1[P][1];
+    S.dtab[k] = csub(shoup_mul(z.x, z.y, (uint32_t)(k - P * digit_values<L>()), q), q);
   }
   __syncthreads();
   if (threadIdx.x == 0) stamp_start(args.stamps);
@@ -458,7 +471,7 @@ cudaError_t prepare_shape() {
   static bool done = false;  // calls are serialised by the engine lock
   if (done) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute(br_kernel<H, GT, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)br_smem_bytes<H, GT>());
+                                       (int)br_smem_bytes<H, GT, L>());
   if (e == cudaSuccess) done = true;
   return e;
 }
@@ -467,7 +480,7 @@ template <int H, int GT, int L = 3>
 cudaError_t launch_shape(const BrArgs &args, int grid, cudaStream_t st) {
   cudaError_t e = prepare_shape<H, GT, L>();
   if (e != cudaSuccess) return e;
-  br_kernel<H, GT, L><<<grid, 2 * H * GT * 32, br_smem_bytes<H, GT>(), st>>>(args);
+  br_kernel<H, GT, L><<<grid, 2 * H * GT * 32, br_smem_bytes<H, GT, L>(), st>>>(args);
   return cudaGetLastError();
 }
 
@@ -480,7 +493,7 @@ int occupancy_shape() {
   }
   int blocks = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, br_kernel<H, GT, L>, 2 * H * GT * 32,
-                                                    br_smem_bytes<H, GT>()) != cudaSuccess) {
+                                                    br_smem_bytes<H, GT, L>()) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
