@@ -569,6 +569,7 @@ int plan_build(Engine &E, const arx_netlist *nl, int keyset, int mode, std::uniq
     CK(P->kscnt.reserve(ks_gate_max * 4));
     CK(cudaMemset(P->kscnt.p, 0, P->kscnt.cap));
   }
+
   const size_t wires = (size_t)nl->num_inputs + nl->num_gates;
   CK(P->wires.reserve(std::max<size_t>(wires, 1) * kWireStride * 4));
   CK(P->brjobs.reserve(std::max<size_t>(br.size(), 1) * sizeof(BrJob)));
@@ -670,6 +671,8 @@ void plan_free(Plan &P) {
   P.brout.release();
   P.outidx.release();
   P.outstage.release();
+  P.kspart.release();
+  P.kscnt.release();
 }
 
 // --------------------------------------------------------------------------

@@ -184,6 +184,24 @@ def test_aliased_buffers(O, keys630, gpu630, torch_cuda):
     assert np.array_equal(h, want_ab)
 
 
+@pytest.mark.parametrize("count", [3, 8, 9, 17, 64, 65])
+def test_key_switch_wave_sizes_bit_exact(O, keys630, gpu630, count):
+    """The split key switch across wave sizes around its split boundaries (the
+    last CTA of each gate reduces the partial sums, counters re-armed for the next
+    call): all gate kinds mixed (MUX: two samples, linear gates: no key rows),
+    every ciphertext equal to the oracle's, twice in a row."""
+    rng = np.random.default_rng(count)
+    types = rng.integers(0, 11, count).astype(np.uint8)
+    types[: min(count, 3)] = [I.MUX, I.NOT, I.AND][: min(count, 3)]
+    xs, ys, zs, ca, cb, cc = _inputs(O, I, keys630, types, 90 + count)
+    want = keys630.ctx.gates(types, ca, cb, cc)
+    for rep in range(2):
+        out = np.zeros_like(ca)
+        arx.bootstrap_gates_ex(types, ca, cb, cc, out, keyset=gpu630)
+        assert np.array_equal(out, want), rep
+    assert np.array_equal(arx.client_decrypt(630, keys630.s, out), _truth(types, xs, ys, zs))
+
+
 def test_empty_and_single_gate(O, keys630, gpu630):
     arx.bootstrap_gates(np.zeros(0, np.uint8), np.zeros((0, 631), np.uint32), np.zeros((0, 631), np.uint32),
                         np.zeros((0, 631), np.uint32))
