@@ -159,8 +159,6 @@ __global__ void __launch_bounds__(kThreads, 1) br_cluster16_kernel(const __grid_
     const uint2 z1 = args.tc.fwd1[P][1], z23 = args.tc.fwd1[P][2 + (Q >> 1)];
     const int jl = 8 * (lane & 3) + (lane >> 2);  // the forward pair's output block (see fwd_quarter_pair)
     const int jf = 32 * fw + jl;
-    const PrimeRT prs[1] = {pr};
-    const uint2 z1s[1] = {z1}, z23s[1] = {z23};
     const FwdPairTw zf = load_fwd_pair(args, P, Q, fw, lane);  // loop-invariant per-lane twiddles
     const bool inv = warp == kInvWarp || warp == kInvWarp + 1;
     const int t = lane + 32 * (warp == kInvWarp + 1 ? 1 : 0);  // position index within the inverse pair
@@ -178,10 +176,13 @@ __global__ void __launch_bounds__(kThreads, 1) br_cluster16_kernel(const __grid_
       for (int k = tid; k < kN; k += kConsThreads)
         A[k] = h == 0 ? 0u : ((((uint32_t)k - shift) & (2u * kN - 1)) < (uint32_t)kN ? kMu : 0u - kMu);
       named_bar(1, kConsThreads);
+      uint32_t acc4[4];  // this thread's column of ACC_h: A[tid + 256 m], kept across CMuxes
+#pragma unroll
+      for (int m = 0; m < 4; ++m) acc4[m] = A[tid + 256 * m];
 
       for (int i = 0; i < n; ++i, ++cm) {
         const uint32_t par = cm & 1u, ph = (cm >> 1) & 1u;
-        make_stage2<L, 1>(D, A, abar[i], z1s, z23s, Q, prs, tid, kConsThreads);
+        make_stage2_col<L>(D, A, acc4, abar[i], z1, z23, Q, pr, tid);
         named_bar(1, kConsThreads);
         if (fwd) {
           uint32_t x[4];
@@ -223,11 +224,12 @@ __global__ void __launch_bounds__(kThreads, 1) br_cluster16_kernel(const __grid_
           // quarter Q of output h in prime P: L local rows and the peer's L rows, at 4 t + e
           // (the slots are read before this CTA's posts below, so before the peer can
           // refill them two CMuxes later)
-          mbar_wait(done1 + par, ph, abort_flag, args.status, kWaitCycles, true);
+          // (the local rows are summed before the wait for the peer's)
           uint32_t y[4] = {0u, 0u, 0u, 0u};
           const int ci = s_j(t);
 #pragma unroll
           for (int r4 = 0; r4 < 2 * L; ++r4) {
+            if (r4 == L) mbar_wait(done1 + par, ph, abort_flag, args.status, kWaitCycles, true);
             const uint4 *sl =
                 reinterpret_cast<const uint4 *>(r4 < L ? own + r4 * kQuarter : slots + (par * L + r4 - L) * kQuarter);
             const uint4 q = sl[ci];
@@ -257,7 +259,7 @@ __global__ void __launch_bounds__(kThreads, 1) br_cluster16_kernel(const __grid_
         {
           const uint32_t *pp = post + par * 2 * 4 * kQuarter;
           const uint32_t *post0[4] = {pp, pp + kQuarter, pp + 2 * kQuarter, pp + 3 * kQuarter};
-          crt_update(A, post0, 4 * kQuarter, args, tid, kConsThreads);
+          crt_update_col(A, acc4, post0, 4 * kQuarter, args, tid);
         }
         named_bar(1, kConsThreads);  // ACC_h updated
       }

@@ -460,6 +460,60 @@ __device__ __forceinline__ void make_stage2(uint32_t *S, const uint32_t *A, uint
   }
 }
 
+// make_stage2 for one prime on a CTA of 256 threads whose thread k holds its
+// column of ACC, acc4[m] = A[k + 256 m], in registers (the previous CMux's CRT
+// pass computed them): only the rotated values come from shared memory.
+template <int L>
+__device__ __forceinline__ void make_stage2_col(uint32_t *S, const uint32_t *A, const uint32_t (&acc4)[4], uint32_t a,
+                                                uint2 z1, uint2 z23, int Qf, const PrimeRT &pr, int k) {
+  static_assert(L == 2 || L == 3, "gadget length");
+  uint32_t u[4][L];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    const uint32_t pos = (uint32_t)k + 256u * m;
+    const uint32_t j = (pos - a) & 2047u;
+    uint32_t v = A[j & 1023u];
+    v = (j & 1024u) ? 0u - v : v;
+    if constexpr (L == 3) {
+      const uint32_t y = v - acc4[m] + kDecOffset;
+      u[m][0] = y >> 25;
+      u[m][1] = (y >> 18) & 0x7Fu;
+      u[m][2] = (y >> 11) & 0x7Fu;
+    } else {
+      const uint32_t y = v - acc4[m] + kDecOffset2;
+      u[m][0] = y >> 22;
+      u[m][1] = (y >> 12) & 0x3FFu;
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < L; ++r) {
+    const uint32_t t0 = shoup_mul(z1.x, z1.y, u[2][r], pr.q);
+    const uint32_t t1 = shoup_mul(z1.x, z1.y, u[3][r], pr.q);
+    const uint32_t s0 = Qf < 2 ? u[0][r] + t0 + pr.dc : u[0][r] - t0 + pr.q2 + pr.dd;
+    const uint32_t s1 = Qf < 2 ? u[1][r] + t1 + pr.dc : u[1][r] - t1 + pr.q2 + pr.dd;
+    const uint32_t t2 = shoup_mul(z23.x, z23.y, s1, pr.q);
+    S[r * 256 + k] = (Qf & 1) ? s0 - t2 + pr.q2 : s0 + t2;
+  }
+}
+
+// crt_update for a CTA of 256 threads whose thread k keeps its column of ACC in
+// acc4 (updated here and stored back to A for the other threads' rotations).
+__device__ __forceinline__ void crt_update_col(uint32_t *A, uint32_t (&acc4)[4], const uint32_t *const (&post0)[4],
+                                               int poff1, const BrArgs &args, int k) {
+  uint32_t t[4], o0[4], o1[4];
+#pragma unroll
+  for (int Q = 0; Q < 4; ++Q) t[Q] = post0[Q][k];
+  inv_last(o0, t, args.tc.psi512[0], args.tc.psi256[0], kQ0);
+#pragma unroll
+  for (int Q = 0; Q < 4; ++Q) t[Q] = post0[Q][k + poff1];
+  inv_last(o1, t, args.tc.psi512[1], args.tc.psi256[1], kQ1);
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    acc4[m] += crt_torus(o0[m], o1[m]);
+    A[k + 256 * m] = acc4[m];
+  }
+}
+
 // The inverse quarter transform on a pair of warps (w = 0, 1 of the pair, t =
 // lane + 32 w): the butterflies, twiddles and stage order of inv_quarter_r, in
 // four register passes of two stages on 4 values per lane (half-lengths 1-2,
