@@ -163,8 +163,8 @@ __global__ void __launch_bounds__(kThreads, 1) br_cluster16_kernel(const __grid_
     const bool inv = warp == kInvWarp || warp == kInvWarp + 1;
     const int t = lane + 32 * (warp == kInvWarp + 1 ? 1 : 0);  // position index within the inverse pair
     const InvPairTw zp = load_inv_pair(args, P, Q, t);
-    uint32_t it = 0, cm = 0;  // tile counter, CMux counter
-    for (int tile = cid; tile < tiles; tile += nclusters, ++it) {
+    uint32_t cm = 0;  // CMux counter over this cluster's tiles
+    for (int tile = cid; tile < tiles; tile += nclusters) {
       const BrJob jb = args.jobs[tile];
       const uint32_t *wa = args.wires + (size_t)jb.ia * kWireStride;
       const uint32_t *wb = args.wires + (size_t)jb.ib * kWireStride;
@@ -182,15 +182,17 @@ __global__ void __launch_bounds__(kThreads, 1) br_cluster16_kernel(const __grid_
 
       for (int i = 0; i < n; ++i, ++cm) {
         const uint32_t par = cm & 1u, ph = (cm >> 1) & 1u;
+        // key row of this CMux: waited for here only for the first CMux; later ones
+        // are waited for during the previous CMux's wait for the partners
+        if (fwd && cm == 0) mbar_wait(full + rr % kStages, 0u, abort_flag, args.status, kWaitCycles, true);
         make_stage2_col<L>(D, A, acc4, abar[i], z1, z23, Q, pr, tid);
         named_bar(1, kConsThreads);
         if (fwd) {
           uint32_t x[4];
           fwd_quarter_pair(x, D + rr * 256, pairbuf + rr * kQuarter, scratch + warp * kQuarter, zf, pr, fw, lane,
                            4 + rr);
-          const uint32_t jc = (it * (uint32_t)n + (uint32_t)i) * (uint32_t)L + (uint32_t)rr;
+          const uint32_t jc = cm * (uint32_t)L + (uint32_t)rr;
           const uint32_t slot = jc % kStages;
-          mbar_wait(full + slot, (jc / kStages) & 1u, abort_flag, args.status, kWaitCycles, true);
           // key row layout: position 32 L + E at word ((E >> 2) * 32 + L) * 4 + (E & 3), so
           // positions 256 Q + 4 j .. + 3 are 16-byte word (j mod 8) * 32 + 8 Q + j / 8
           const uint4 *Bown = reinterpret_cast<const uint4 *>(ring + slot * kRowWords + h * kN);
@@ -254,8 +256,13 @@ __global__ void __launch_bounds__(kThreads, 1) br_cluster16_kernel(const __grid_
           const uint32_t dst = rank ^ (2u * (uint32_t)(warp + 1));
           bulk_s2peer(map_peer(smem_u32(pq), dst), pq, kQuarter * 4u, map_peer(smem_u32(done2 + par), dst));
         }
+        if (fwd && (i + 1 < n || tile + nclusters < tiles)) {  // the next CMux's key row
+          const uint32_t jn = (cm + 1u) * (uint32_t)L + (uint32_t)rr;
+          mbar_wait(full + jn % kStages, (jn / kStages) & 1u, abort_flag, args.status, kWaitCycles, true);
+        }
+        // every thread waits for the partners' quarters itself (the local one is
+        // behind barrier 7), so no barrier is needed before the CRT pass
         mbar_wait(done2 + par, ph, abort_flag, args.status, kWaitCycles, true);
-        named_bar(1, kConsThreads);  // all four quarters of both primes posted
         {
           const uint32_t *pp = post + par * 2 * 4 * kQuarter;
           const uint32_t *post0[4] = {pp, pp + kQuarter, pp + 2 * kQuarter, pp + 3 * kQuarter};
