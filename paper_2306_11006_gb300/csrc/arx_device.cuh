@@ -19,7 +19,9 @@
 // bit-reversed in, natural out, then the output twist psi^-j): pass 1 on
 // a[32 lane + e] with uniform twiddles, transpose, pass 2 with per-lane twiddles.
 // Both directions grow lazily by < 2q per stage with no correction: the forward
-// starts below 3q + 128 and ends below 22q, the inverse starts below 12q (six
+// starts below 3q + 1024 after its first stage (or 4q + 128 after the first two,
+// taken from digit tables for Bg = 2^7) and ends below 22q, the inverse starts
+// below 12q (six
 // Montgomery products) and ends below 32q < 2^32.  The twist's Shoup product and
 // one conditional subtraction bring the result to [0, q).
 #pragma once
@@ -95,20 +97,39 @@ __device__ __forceinline__ void ct_bfly(uint32_t &x, uint32_t &y, uint2 z, const
 __device__ __forceinline__ int swz(int r, int c) { return r * 32 + ((((c >> 2) ^ (r & 7))) << 2) + (c & 3); }
 
 // ---- warp transforms ----------------------------------------------------
-// Forward.  kDigits: x[e] holds raw gadget digits u = d + Bg/2 in [0, Bg) of
-// a[lane + 32 e]; the -Bg/2 offsets ride on the first stage's constants, and
-// the first stage's products zeta[1] u come from dtab[u] (zeta[1] u mod q,
-// fully reduced, built once per CTA: a shared-memory load instead of a Shoup
-// product).  Otherwise x[e] < q.  Output: x[e] = A[32 lane + e] < 22 q.
-template <bool kDigits>
+// Forward.  kDig = 0: x[e] < q.  kDig = 1: x[e] holds raw gadget digits u =
+// d + Bg/2 in [0, Bg) of a[lane + 32 e]; the -Bg/2 offsets ride on the first
+// stage's constants, and the first stage's products zeta[1] u come from dtab[u]
+// (zeta[1] u mod q, fully reduced, built once per CTA: a shared-memory load
+// instead of a Shoup product).  kDig = 2 (7-bit digits, Bg = 2^7): the first two
+// stages at once, as four sums of table products -- with z1 = zeta[1] and z2,
+// z3 = zeta[2], zeta[3], the radix-4 group (u0, u1, u2, u3) = x[e, e+8, e+16,
+// e+24] gives u0 + z1 u2 +- (z2 u1 + z2 z1 u3) and u0 - z1 u2 +- (z3 u1 - z3 z1 u3),
+// the five products from dtab[t][u], t = (z1, z2, z2 z1, z3, z3 z1), and the
+// digit offsets and 2q (outputs 1 .. 3, which subtract two table values) from
+// dk[0 .. 3]: each output is below 4q + Bg before stage 3.  Output: x[e] =
+// A[32 lane + e] < 22 q.
+template <int kDig>
 __device__ __forceinline__ void ntt_fwd(uint32_t (&x)[32], uint32_t *xbuf, const uint2 *tw1,
                                         const uint2 *__restrict__ tw2, const PrimeRT &pr, int lane,
-                                        const uint32_t *dtab = nullptr) {
-  {
+                                        const uint32_t *dtab = nullptr, const uint32_t *dk = nullptr) {
+  if constexpr (kDig == 2) {
+    const uint32_t k0 = dk[0], k1 = dk[1], k2 = dk[2], k3 = dk[3];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const uint32_t u0 = x[e], u1 = x[e + 8], u2 = x[e + 16], u3 = x[e + 24];
+      const uint32_t a = dtab[u2], b = dtab[128 + u1], c = dtab[256 + u3], d = dtab[384 + u1], f = dtab[512 + u3];
+      const uint32_t s = u0 + a, t = u0 - a;  // t wraps; every output below is a non-negative integer < 2^32
+      x[e] = s + b + c + k0;
+      x[e + 8] = s - b - c + k1;
+      x[e + 16] = t + d - f + k2;
+      x[e + 24] = t - d + f + k3;
+    }
+  } else {
     const uint2 z = tw1[1];
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
-      if (kDigits) {
+      if (kDig == 1) {
         const uint32_t t = dtab[x[e + 16]];
         const uint32_t u = x[e];
         x[e] = u + t + pr.dc;
@@ -119,7 +140,7 @@ __device__ __forceinline__ void ntt_fwd(uint32_t (&x)[32], uint32_t *xbuf, const
     }
   }
 #pragma unroll
-  for (int s = 1; s < 5; ++s) {
+  for (int s = kDig == 2 ? 2 : 1; s < 5; ++s) {
     const int lr = 16 >> s;
 #pragma unroll
     for (int e = 0; e < 32; ++e) {

@@ -31,6 +31,7 @@ struct TwiddleConst {
   uint32_t dig_d[2];      // (64 zeta[1] - 64) mod q
   uint32_t dig_c2[2];     // the same for 10-bit digits (gadget l = 2, Bg = 2^10): (-512 - 512 zeta[1]) mod q
   uint32_t dig_d2[2];     // (512 zeta[1] - 512) mod q
+  uint32_t dig4[2][4];    // first two forward stages of raw 7-bit digits: the constant parts (ntt_fwd<2>)
   uint2 psi512[2];        // psi^-512 and psi^-256 (last stages of the split inverse)
   uint2 psi256[2];
 };

@@ -152,7 +152,7 @@ __device__ __forceinline__ void make_digits(uint32_t *dig, const uint32_t *A, ui
 
 struct BrShared {
   uint32_t *ring;     // kStages x kChunkWords
-  uint32_t *dtab;     // [prime][Bg]: zeta[1] u mod q for every digit value u (first forward stage)
+  uint32_t *dtab;     // [prime][digit_tab_words]: table products of digit values (see ntt_fwd)
   uint32_t *acc;      // GT x [2][N]
   uint32_t *dig;      // GT x [2][N] packed gadget digits
   uint32_t *scratch;  // consumer warps x kScratch
@@ -173,10 +173,16 @@ __host__ __device__ constexpr int scratch_words() { return (H == 1 ? 1 : 2) * kX
 template <int L>
 __host__ __device__ constexpr int digit_values() { return L == 3 ? 128 : 1024; }
 
+// Words of a prime's digit tables: for L = 3 the products of the first two
+// forward stages, [z1, z2, z2 z1, z3, z3 z1][u] (ntt_fwd<2>); for L = 2 zeta[1] u
+// (ntt_fwd<1>).
+template <int L>
+__host__ __device__ constexpr int digit_tab_words() { return L == 3 ? 5 * 128 : 1024; }
+
 template <int H, int GT, int L = 3>
 constexpr size_t br_fixed_bytes() {
   return (size_t)GT * 4 * kN * 4 + (size_t)2 * H * GT * scratch_words<H>() * 4 + (size_t)GT * kAbarPitch * 2 +
-         (size_t)2 * digit_values<L>() * 4 + 2 * 8 * 8 + 16;
+         (size_t)2 * digit_tab_words<L>() * 4 + 2 * 8 * 8 + 16;
 }
 
 // Ring depth: as many key rows in flight as shared memory allows, 4..8.
@@ -197,7 +203,7 @@ __device__ __forceinline__ BrShared br_carve(uint8_t *smem) {
   BrShared s;
   s.ring = reinterpret_cast<uint32_t *>(smem);
   s.dtab = s.ring + kStages * kChunkWords;
-  s.acc = s.dtab + 2 * digit_values<L>();
+  s.acc = s.dtab + 2 * digit_tab_words<L>();
   s.dig = s.acc + GT * 2 * kN;
   s.scratch = s.dig + GT * 2 * kN;
   s.abar = reinterpret_cast<uint16_t *>(s.scratch + 2 * H * GT * scratch_words<H>());
@@ -311,7 +317,7 @@ __device__ __forceinline__ void br_consumer(const BrShared &S, const BrArgs &arg
 #pragma unroll
           for (int e = 0; e < 32; ++e) x[e] = (dc[lane + 32 * e] >> sh) & 0xFFFFu;
         }
-        ntt_fwd<true>(x, myscr, tw1f, tw2f, pr, lane, S.dtab + P * digit_values<L>());
+        ntt_fwd<L == 3 ? 2 : 1>(x, myscr, tw1f, tw2f, pr, lane, S.dtab + P * digit_tab_words<L>(), args.tc.dig4[P]);
         // MAC with the NTT-domain key row staged in the ring.
         const uint32_t jc = (it * (uint32_t)n + (uint32_t)i) * (uint32_t)kRows + (uint32_t)r;
         const uint32_t slot = jc % kStages;
@@ -438,11 +444,16 @@ __global__ void __launch_bounds__(2 * H * GT * 32, 1) br_kernel(const __grid_con
     *S.abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  for (int k = threadIdx.x; k < 2 * digit_values<L>(); k += blockDim.x) {  // zeta[1] u mod q per prime
-    const int P = k / digit_values<L>();
-    const uint32_t q = P ? kQ1 : kQ0;
-    const uint2 z = args.tc.fwd1[P][1];
-    S.dtab[k] = csub(shoup_mul(z.x, z.y, (uint32_t)(k - P * digit_values<L>()), q), q);
+  for (int k = threadIdx.x; k < 2 * digit_tab_words<L>(); k += blockDim.x) {  // digit tables per prime
+    const int P = k / digit_tab_words<L>(), j = k - P * digit_tab_words<L>();
+    const uint64_t q = P ? kQ1 : kQ0;
+    uint64_t z = args.tc.fwd1[P][1].x;  // L = 2: zeta[1]
+    if (L == 3) {
+      const uint64_t z1 = args.tc.fwd1[P][1].x, z2 = args.tc.fwd1[P][2].x, z3 = args.tc.fwd1[P][3].x;
+      const int t = j >> 7;
+      z = t == 0 ? z1 : t == 1 ? z2 : t == 2 ? z2 * z1 % q : t == 3 ? z3 : z3 * z1 % q;
+    }
+    S.dtab[k] = (uint32_t)(z * (uint64_t)(j & (digit_values<L>() - 1)) % q);
   }
   __syncthreads();
   if (threadIdx.x == 0) stamp_start(args.stamps);

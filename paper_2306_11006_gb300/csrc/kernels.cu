@@ -45,7 +45,7 @@ __device__ void bsk_poly_to_ntt(const uint32_t *src, uint32_t *dst, uint32_t *xb
     const int32_t m = v % (int32_t)q;
     x[e] = (uint32_t)(m < 0 ? m + (int32_t)q : m);
   }
-  ntt_fwd<false>(x, xbuf, tc.fwd1[P], tg->fwd2[P], pr, lane);
+  ntt_fwd<0>(x, xbuf, tc.fwd1[P], tg->fwd2[P], pr, lane);
 #pragma unroll
   for (int e = 0; e < 32; ++e) {
     const uint32_t v = x[e] % q;

@@ -77,6 +77,17 @@ void fill(int P, uint64_t q, TwiddleConst *tc, TwiddleGlobal *tg) {
   tc->dig_d[P] = (uint32_t)((64 * zeta[1] % q + q - 64) % q);
   tc->dig_c2[P] = (uint32_t)((2 * q - 512 - 512 * zeta[1] % q) % q);
   tc->dig_d2[P] = (uint32_t)((512 * zeta[1] % q + q - 512) % q);
+  {  // stages 1 and 2 on raw digits u = d + 64: output j carries -64 (its sum of
+     // +-1, +-z1, +-z2 or z3, +-z2 z1 or z3 z1); outputs 1 .. 3 add 2q (see ntt_fwd)
+    const uint64_t z1 = zeta[1], z2 = zeta[2], z3 = zeta[3], z21 = z2 * z1 % q, z31 = z3 * z1 % q;
+    auto off = [q](uint64_t plus, uint64_t minus) {  // 64 (minus - plus) mod q
+      return (uint32_t)((64 * (minus % q) % q + q - 64 * (plus % q) % q) % q);
+    };
+    tc->dig4[P][0] = off(1 + z1 + z2 + z21, 0);
+    tc->dig4[P][1] = (uint32_t)(2 * q) + off(1 + z1, z2 + z21);
+    tc->dig4[P][2] = (uint32_t)(2 * q) + off(1 + z3, z1 + z31);
+    tc->dig4[P][3] = (uint32_t)(2 * q) + off(1 + z31, z1 + z3);
+  }
   // forward pass 2, per lane: stage s (length 16 >> s) has 2^s blocks per lane;
   // block b of lane l is zeta index 2^s (32 + l) + b, stored at [(2^s - 1 + b)][l].
   for (int s = 0; s < 5; ++s)
