@@ -15,15 +15,15 @@
 // order in, bit-reversed order out): pass 1 (lengths 512..32) on
 // x[e] = a[lane + 32 e] with warp-uniform twiddles from the kernel parameter bank,
 // a swizzled shared-memory transpose, pass 2 (lengths 16..1) on a[32 lane + e]
-// with per-lane twiddles.  Inverse (cyclic Cooley-Tukey DIT with omega^-1,
-// bit-reversed in, natural out, then the output twist psi^-j): pass 1 on
-// a[32 lane + e] with uniform twiddles, transpose, pass 2 with per-lane twiddles.
-// Both directions grow lazily by < 2q per stage with no correction: the forward
-// starts below 3q + 1024 after its first stage (or 4q + 128 after the first two,
-// taken from digit tables for Bg = 2^7) and ends below 22q, the inverse starts
-// below 12q (six
-// Montgomery products) and ends below 32q < 2^32.  The twist's Shoup product and
-// one conditional subtraction bring the result to [0, q).
+// with per-lane twiddles.  Inverse of the warp transforms (ntt_inv_gs):
+// Gentleman-Sande with the psi^-1 twist merged into its twiddles, bit-reversed
+// in, natural out, pass 1 (half-lengths 1..16) on a[32 lane + e] with per-lane
+// twiddles, transpose, pass 2 (32..512) with warp-uniform ones; the split
+// transforms of the cluster kernels keep a cyclic inverse and a separate twist.
+// The forward grows lazily by < 2q per stage with no correction: it starts below
+// 3q + 1024 after its first stage (or 4q + 128 after the first two, taken from
+// digit tables for Bg = 2^7) and ends below 22q.  The inverse starts below 12q
+// (six Montgomery products) and reduces every butterfly output to [0, 2q).
 #pragma once
 #include <cstdint>
 
@@ -175,17 +175,47 @@ __device__ __forceinline__ void ntt_fwd(uint32_t (&x)[32], uint32_t *xbuf, const
   }
 }
 
-// Inverse (the 1/N factor rides on the stored key): x[e] = A[32 lane + e] < 12 q
-// -> x[e] = a[lane + 32 e] in [0, 2q) (what crt_torus takes).
-__device__ __forceinline__ void ntt_inv(uint32_t (&x)[32], uint32_t *xbuf, const uint2 *tw1,
-                                        const uint2 *__restrict__ tw2, const uint2 *__restrict__ twist,
-                                        const PrimeRT &pr, int lane) {
+// Gentleman-Sande butterfly of the merged inverse: (x, y) -> (x + y, (x - y) z),
+// both in [0, 2q).  kFirst: x, y < 12q (the sum of six Montgomery products),
+// else x, y < 2q.
+template <bool kFirst>
+__device__ __forceinline__ void gs_bfly(uint32_t &x, uint32_t &y, uint2 z, const PrimeRT &pr) {
+  uint32_t s = x + y;
+  const uint32_t d = x - y + (kFirst ? 6u * pr.q2 : pr.q2);
+  if (kFirst) {
+    s = csub(s, 8u * pr.q2);  // < 24q -> < 16q
+    s = csub(s, 4u * pr.q2);
+    s = csub(s, 2u * pr.q2);
+  }
+  x = csub(s, pr.q2);
+  y = shoup_mul(z.x, z.y, d, pr.q);
+}
+
+// Inverse with the output twist merged into the butterflies (Gentleman-Sande,
+// psi^-1 powers: no separate twist pass; the 1/N factor rides on the stored
+// key).  Pass 1 (half-lengths 1..16) on a[32 lane + e] with per-lane twiddles
+// gs1, transpose, pass 2 (half-lengths 32..512) on a[lane + 32 e] with the
+// warp-uniform gs2 (kernel parameter bank).  In: x[e] = A[32 lane + e] < 12 q
+// (bit-reversed spectral order, as ntt_fwd leaves it).  Out: x[e] = a[lane +
+// 32 e] in [0, 2q) (what crt_torus takes); every butterfly output is reduced to
+// [0, 2q) (one conditional subtraction on the sum, the Shoup product on the
+// difference).
+__device__ __forceinline__ void ntt_inv_gs(uint32_t (&x)[32], uint32_t *xbuf, const uint2 *__restrict__ gs1,
+                                           const uint2 *gs2, const PrimeRT &pr, int lane) {
+  constexpr int kOff[5] = {0, 16, 24, 28, 30};
 #pragma unroll
-  for (int t = 0; t < 5; ++t) {
-    const int h = 1 << t;  // half-length 1, 2, 4, 8, 16
+  for (int s = 0; s < 5; ++s) {
+    const int t = 1 << s;  // half-length 1, 2, 4, 8, 16
+    uint2 z;
 #pragma unroll
     for (int e = 0; e < 32; ++e) {
-      if ((e & h) == 0) ct_bfly(x[e], x[e + h], tw1[(h - 1) + (e & (h - 1))], pr);
+      if ((e & t) == 0) {
+        if ((e & (2 * t - 1)) == 0) z = __ldg(gs1 + (kOff[s] + e / (2 * t)) * 32 + lane);
+        if (s == 0)
+          gs_bfly<true>(x[e], x[e + t], z, pr);
+        else
+          gs_bfly<false>(x[e], x[e + t], z, pr);
+      }
     }
   }
   __syncwarp();
@@ -201,13 +231,8 @@ __device__ __forceinline__ void ntt_inv(uint32_t (&x)[32], uint32_t *xbuf, const
     const int hr = 1 << s;  // half-length / 32: 1, 2, 4, 8, 16
 #pragma unroll
     for (int e = 0; e < 32; ++e) {
-      if ((e & hr) == 0) ct_bfly(x[e], x[e + hr], __ldg(tw2 + ((hr - 1) + (e & (hr - 1))) * 32 + lane), pr);
+      if ((e & hr) == 0) gs_bfly<false>(x[e], x[e + hr], gs2[16 / hr + e / (2 * hr)], pr);
     }
-  }
-#pragma unroll
-  for (int e = 0; e < 32; ++e) {
-    const uint2 w = __ldg(twist + e * 32 + lane);
-    x[e] = shoup_mul(w.x, w.y, x[e], pr.q);
   }
 }
 

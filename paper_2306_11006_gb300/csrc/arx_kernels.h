@@ -20,8 +20,10 @@ constexpr uint32_t kQ1 = 134203393u;
 
 // Twiddles.  Forward zeta[k] = psi^bitrev10(k) (k = 1..1023), psi a primitive
 // 2048-th root of unity mod q; the stage with m blocks uses zeta[m + block].
-// Inverse: omega = psi^2, the DIT stage of half-length h uses omega^-(j 512 / h)
-// for the j-th pair of a block, then the output twist psi^-p.  Every entry is
+// Inverse of the split transforms: omega = psi^2, the DIT stage of half-length h
+// uses omega^-(j 512 / h) for the j-th pair of a block, then the output twist
+// psi^-p; of the warp transforms: Gentleman-Sande, the stage of half-length t
+// uses psi^-bitrev10(512 / t + block).  Every entry is
 // (w, floor(w 2^32 / q)).  The warp-uniform ones travel in the kernel parameter
 // block (constant bank), the per-lane ones in global memory.
 struct TwiddleConst {
@@ -32,6 +34,7 @@ struct TwiddleConst {
   uint32_t dig_c2[2];     // the same for 10-bit digits (gadget l = 2, Bg = 2^10): (-512 - 512 zeta[1]) mod q
   uint32_t dig_d2[2];     // (512 zeta[1] - 512) mod q
   uint32_t dig4[2][4];    // first two forward stages of raw 7-bit digits: the constant parts (ntt_fwd<2>)
+  uint2 gsi2[2][32];      // merged inverse pass 2 (half-lengths 32..512): psi^-bitrev10(k), k = 1..31
   uint2 psi512[2];        // psi^-512 and psi^-256 (last stages of the split inverse)
   uint2 psi256[2];
 };
@@ -39,7 +42,7 @@ struct TwiddleConst {
 struct TwiddleGlobal {
   uint2 fwd2[2][31 * 32];   // forward pass 2, per lane: [(2^s - 1) + block][lane]
   uint2 inv2[2][31 * 32];   // inverse pass 2, per lane: [(h/32 - 1) + j mod (h/32)][lane]
-  uint2 twist[2][32 * 32];  // inverse output twist psi^-p, p = lane + 32 e: [e][lane]
+  uint2 gsi1[2][31 * 32];   // merged inverse pass 1 (half-lengths 1..16), per lane: [off_s + block][lane]
   // split transforms of the cluster kernel
   uint2 fwdh[2][2][15 * 32];  // forward pass 2 of half w: [prime][w][(2^s - 1) + block][lane]
   uint2 fwdc[2][4][7 * 32];   // forward middle pass of quarter Q (lengths 32, 16, 8): [prime][Q][(2^s - 1) + block][lane]

@@ -268,10 +268,8 @@ __device__ __forceinline__ void br_consumer(const BrShared &S, const BrArgs &arg
     pr.dd = args.tc.dig_d2[P];
   }
   const uint2 *tw1f = args.tc.fwd1[P];
-  const uint2 *tw1i = args.tc.inv1[P];
   const uint2 *tw2f = args.tg->fwd2[P];
-  const uint2 *tw2i = args.tg->inv2[P];
-  const uint2 *twist = args.tg->twist[P];
+  const uint2 *gsi1 = args.tg->gsi1[P];
   const int tiles = (args.num_jobs + GT - 1) / GT;
   const uint32_t rows = cta_rows<GT, L>(args);
   uint32_t it = 0;
@@ -354,7 +352,7 @@ __device__ __forceinline__ void br_consumer(const BrShared &S, const BrArgs &arg
         // both outputs: one inverse code path, the accumulators swapped between uses
 #pragma unroll 1
         for (int c = 0; c < 2; ++c) {
-          ntt_inv(acc0, myscr, tw1i, tw2i, twist, pr, lane);
+          ntt_inv_gs(acc0, myscr, gsi1, args.tc.gsi2[P], pr, lane);
 #pragma unroll
           for (int e = 0; e < 32; ++e) {
             const uint32_t t = acc0[e];
@@ -399,7 +397,7 @@ __device__ __forceinline__ void br_consumer(const BrShared &S, const BrArgs &arg
 #pragma unroll
             for (int e = 0; e < 32; ++e) acc0[e] += src[e * 32 + lane];
           }
-          ntt_inv(acc0, half, tw1i, tw2i, twist, pr, lane);
+          ntt_inv_gs(acc0, half, gsi1, args.tc.gsi2[P], pr, lane);
           __syncwarp();
 #pragma unroll
           for (int e = 0; e < 16; ++e) half[e * 32 + lane] = P ? acc0[e] : acc0[16 + e];

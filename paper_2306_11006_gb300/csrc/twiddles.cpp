@@ -2,10 +2,12 @@
 //
 // Forward (negacyclic, merged twist): zeta[k] = psi^bitrev10(k) for k = 1..1023,
 // psi a primitive 2048-th root of unity mod q (psi^1024 = -1); the stage with m
-// blocks uses zeta[m + block].  Inverse (cyclic DIT on the bit-reversed
-// spectrum, omega = psi^2): the stage of half-length h uses omega^-(j 512 / h) for
-// the j-th pair of each block, followed by the twist psi^-p at output p.  Every
-// entry carries its Shoup companion floor(w 2^32 / q).
+// blocks uses zeta[m + block].  Inverse of the warp transforms (Gentleman-Sande,
+// merged twist): the stage of half-length t uses psi^-bitrev10(512 / t + block).
+// Inverse of the split transforms (cyclic DIT on the bit-reversed spectrum,
+// omega = psi^2): the stage of half-length h uses omega^-(j 512 / h) for the j-th
+// pair of each block, followed by the twist psi^-p at output p.  Every entry
+// carries its Shoup companion floor(w 2^32 / q).
 //
 // Split transforms of the cluster kernel.  Forward: two warps per transform, half
 // w holds positions 512 w .. 512 w + 511; in pass 2 lane l holds the 16
@@ -138,9 +140,24 @@ void fill(int P, uint64_t q, TwiddleConst *tc, TwiddleGlobal *tg) {
     for (int k = 0; k < 256; ++k) tg->fint[P][Q][k] = entry(pw(psi_inv, (uint64_t)cQ[Q] * k, q), q);
   tc->psi512[P] = entry(pw(psi_inv, 512, q), q);
   tc->psi256[P] = entry(pw(psi_inv, 256, q), q);
-  // output twist psi^-p at p = lane + 32 e
-  for (int e = 0; e < 32; ++e)
-    for (int lane = 0; lane < 32; ++lane) tg->twist[P][e * 32 + lane] = entry(pw(psi_inv, lane + 32 * e, q), q);
+  // merged inverse (Gentleman-Sande, bit-reversed in, natural out): the butterfly
+  // of half-length t on block i (positions 2 t i .. 2 t i + 2t - 1) takes
+  // psi^-bitrev10(512 / t + i).  Pass 1 (t = 1..16, lane l holds positions
+  // 32 l + e): block i = l 16 / t + b, b < 16 / t, stored at [off_s + b][l],
+  // off = 0, 16, 24, 28, 30; pass 2 (t = 32..512, positions l + 32 e): the block
+  // does not depend on the lane, index 512 / t + e / (t / 16) in gsi2.
+  {
+    const int off[5] = {0, 16, 24, 28, 30};
+    for (int s = 0; s < 5; ++s) {
+      const int t = 1 << s;
+      for (int b = 0; b < 16 / t; ++b)
+        for (int lane = 0; lane < 32; ++lane)
+          tg->gsi1[P][(off[s] + b) * 32 + lane] =
+              entry(pw(psi_inv, bitrev10((uint32_t)(512 / t + lane * (16 / t) + b)), q), q);
+    }
+    tc->gsi2[P][0] = entry(1, q);
+    for (uint32_t k = 1; k < 32; ++k) tc->gsi2[P][k] = entry(pw(psi_inv, bitrev10(k), q), q);
+  }
 }
 
 }  // namespace
