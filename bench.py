@@ -431,7 +431,7 @@ def measure_plan(arx, torch, nl, desc, args, n, l, keyset, kr, dev, stream, step
     # roofline of the dominant kernels (blind rotation), timed launch by launch
     br_ms, ks_ms, br_l, ks_l = plan.profile(ct_in)
     waves_of = {}
-    for H, GT, jobs in plan.shapes():
+    for _, H, GT, jobs in plan.launches():
         if jobs:
             k = kernel_name(H, GT)
             waves_of[k] = waves_of.get(k, 0) + 1

@@ -200,7 +200,8 @@ int arx_plan_destroy(int plan);
 /* Describe a plan: waves, blind rotations, gates (any may be NULL). */
 int arx_plan_info(int plan, uint32_t *waves, uint64_t *bootstraps, uint64_t *gates);
 /* Launch shape of each wave of a plan (what the autotuner or the override
- * chose when the plan was created): for wave w < min(cap, waves), H[w] and
+ * chose when the plan was created; for a wave split over two launches, see
+ * arx_plan_launches, the shape of its first): for wave w < min(cap, waves), H[w] and
  * GT[w] as in arx_set_launch_shape ((96, 1) / (48, 1) / (24, 1) / (12, 1): the
  * sixteen- / eight- / four- / two-CTA cluster kernels; for key sets with
  * gadget l = 2, (80, 1) / (40, 1) their sixteen- / eight-CTA kernels and
@@ -209,6 +210,13 @@ int arx_plan_info(int plan, uint32_t *waves, uint64_t *bootstraps, uint64_t *gat
  * launches no blind rotation).  Host arrays; any may be NULL.  Returns the
  * number of waves.  No counterpart in the paper: introspection only. */
 int arx_plan_shapes(int plan, uint32_t *H, uint32_t *GT, uint32_t *jobs, uint32_t cap);
+/* Every blind-rotation launch of a plan in launch order: an autotuned (graph
+ * mode, gadget l = 3) wave whose width is not a whole number of rounds of any
+ * shape may run as two launches, rounds of a throughput shape and its remainder
+ * on the shape that suits the remainder.  For launch k < min(cap, launches):
+ * wave[k], H[k], GT[k] (as arx_plan_shapes) and jobs[k].  Host arrays; any may
+ * be NULL.  Returns the number of launches.  Introspection only. */
+int arx_plan_launches(int plan, uint32_t *wave, uint32_t *H, uint32_t *GT, uint32_t *jobs, uint32_t cap);
 /* Copy wires of the plan's most recent evaluation: out[k] = wire ids[k]
  * ([count][n+1]; ids host array, out host or device).  Synchronous.  Lets a
  * caller inspect or checkpoint intermediate ciphertexts. */

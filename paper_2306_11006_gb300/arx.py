@@ -62,6 +62,7 @@ SIGNATURES = {
     "arx_plan_destroy": (_i, [_i]),
     "arx_plan_info": (_i, [_i, _vp, _vp, _vp]),
     "arx_plan_shapes": (_i, [_i, _vp, _vp, _vp, _u32]),
+    "arx_plan_launches": (_i, [_i, _vp, _vp, _vp, _vp, _u32]),
     "arx_plan_wires": (_i, [_i, _vp, _sz, _vp]),
     "arx_set_launch_shape": (_i, [_i, _i]),
     "arx_plan_profile": (_i, [_i, _vp, _vp, _vp, _vp, _vp]),
@@ -261,6 +262,13 @@ class Plan:
         H, GT, J = (np.zeros(cap, np.uint32) for _ in range(3))
         w = _check(lib().arx_plan_shapes(self.id, _ptr(H), _ptr(GT), _ptr(J), cap))
         return [(int(H[k]), int(GT[k]), int(J[k])) for k in range(min(w, cap))]
+
+    def launches(self):
+        """Every blind-rotation launch: list of (wave, H, GT, blind rotations)."""
+        cap = 2 * max(self.waves, 1)
+        W, H, GT, J = (np.zeros(cap, np.uint32) for _ in range(4))
+        k = _check(lib().arx_plan_launches(self.id, _ptr(W), _ptr(H), _ptr(GT), _ptr(J), cap))
+        return [(int(W[i]), int(H[i]), int(GT[i]), int(J[i])) for i in range(min(k, cap))]
 
     def profile(self, ct_in):
         """One wave-by-wave run timed per launch: (br_ms, ks_ms, br_launches, ks_launches)."""

@@ -237,32 +237,69 @@ BrShape ShapePolicy::for_gadget(int l, BrShape s, int jobs) const {
 BrShape ShapePolicy::pick(int jobs, int n) const {
   if (forced.H) return forced;
   if (tune.empty() || tuned_n != n) return heuristic(jobs);
-  double best = 1e300;
   BrShape out = tune.front().shape;
+  launch_cost(jobs, &out);
+  return out;
+}
+
+double ShapePolicy::launch_cost(int jobs, BrShape *s) const {
+  double best = 1e300;
   for (const TuneEntry &t : tune) {
     const int waves = (jobs + t.gates_per_wave - 1) / t.gates_per_wave;
     const double cost = waves * t.wave_ms_per_cmux;
     if (cost < best * 0.999) {
       best = cost;
-      out = t.shape;
+      if (s) *s = t.shape;
     }
   }
-  return out;
+  return best;
+}
+
+// A persistent launch costs whole rounds of its shape, so a level whose width is
+// not a multiple of any shape's round pays a full round for its remainder; here
+// the remainder may take a second launch on a shape sized for it (the 912-gate
+// rounds of (1, 6) and 8 left over: a sixteen-CTA launch for the 8).
+double ShapePolicy::split(int jobs, BrShape *bulk, int *bulk_jobs, BrShape *tail) const {
+  BrShape s1 = tune.empty() ? BrShape{1, 1} : tune.front().shape;
+  double best = launch_cost(jobs, &s1);
+  *bulk = s1;
+  *bulk_jobs = jobs;
+  *tail = BrShape{0, 0};
+  for (const TuneEntry &t : tune) {
+    if (is_cluster_shape(t.shape) || t.gates_per_wave <= 0) continue;
+    for (long long k = 1; k * t.gates_per_wave < jobs; ++k) {
+      BrShape s2 = t.shape;
+      const double c = k * t.wave_ms_per_cmux + launch_cost(jobs - (int)(k * t.gates_per_wave), &s2);
+      if (c < best * 0.999) {
+        best = c;
+        *bulk = t.shape;
+        *bulk_jobs = (int)(k * t.gates_per_wave);
+        *tail = s2;
+      }
+    }
+  }
+  return best;
 }
 
 int ShapePolicy::free_capacity(int jobs, int n, int l) const {
   if (jobs <= 0) return 0;
   if (forced.H) return jobs;
   if (l == 3 && !tune.empty() && tuned_n == n) {
-    // cost of the best shape for `jobs` (as pick), then the widest launch of any
-    // shape within that cost
-    double best = 1e300;
-    for (const TuneEntry &t : tune)
-      best = std::min(best, ((jobs + t.gates_per_wave - 1) / t.gates_per_wave) * t.wave_ms_per_cmux);
+    // cost of the level as split runs it, then the widest level within that cost:
+    // k rounds of a throughput shape and whole rounds of any shape for the rest
+    BrShape b, t2;
+    int bj = 0;
+    const double budget = split(jobs, &b, &bj, &t2) * (1.0 + 1e-9);
     long long cap = jobs;
-    for (const TuneEntry &t : tune) {
-      const long long rounds = (long long)(best / t.wave_ms_per_cmux * (1.0 + 1e-9));
-      cap = std::max(cap, rounds * t.gates_per_wave);
+    for (const TuneEntry &t1 : tune) {
+      const bool bulk_ok = !is_cluster_shape(t1.shape) && t1.wave_ms_per_cmux > 0.0;
+      for (long long k = 0; k == 0 || (bulk_ok && k * t1.wave_ms_per_cmux <= budget); ++k) {
+        const double rest = budget - k * t1.wave_ms_per_cmux;
+        long long tail = 0;
+        for (const TuneEntry &t : tune)
+          if (t.wave_ms_per_cmux > 0.0) tail = std::max(tail, (long long)(rest / t.wave_ms_per_cmux) * t.gates_per_wave);
+        cap = std::max(cap, k * t1.gates_per_wave + tail);
+      }
     }
     return (int)std::min<long long>(cap, INT_MAX / 2);
   }
@@ -554,10 +591,23 @@ int plan_build(Engine &E, const arx_netlist *nl, int keyset, int mode, std::uniq
   }
   P->bootstraps = br.size();
   size_t ks_part_max = 0, ks_gate_max = 0;
+  const bool tuned = mode == ARX_MODE_GRAPH && P->l == 3 && !E.policy.forced.H && !E.policy.tune.empty() &&
+                     E.policy.tuned_n == P->n;
   for (Level &L : P->levels) {
-    L.shape = E.policy.for_gadget(
-        P->l, mode == ARX_MODE_GRAPH ? E.policy.pick(L.br_cnt, P->n) : E.policy.heuristic(L.br_cnt), L.br_cnt);
-    L.grid = E.policy.grid(L.shape, std::max(1, L.br_cnt));
+    if (tuned && L.br_cnt > 0) {  // autotuned, possibly as a bulk launch and a tail launch
+      BrShape tail{0, 0};
+      int bulk_jobs = L.br_cnt;
+      E.policy.split(L.br_cnt, &L.shape, &bulk_jobs, &tail);
+      if (tail.H && bulk_jobs > 0 && bulk_jobs < L.br_cnt) {
+        L.br_split = bulk_jobs;
+        L.shape2 = tail;
+        L.grid2 = E.policy.grid(tail, L.br_cnt - bulk_jobs);
+      }
+    } else {
+      L.shape = E.policy.for_gadget(
+          P->l, mode == ARX_MODE_GRAPH ? E.policy.pick(L.br_cnt, P->n) : E.policy.heuristic(L.br_cnt), L.br_cnt);
+    }
+    L.grid = E.policy.grid(L.shape, std::max(1, L.br_split ? L.br_split : L.br_cnt));
     L.ks_splits = ks_splits(L.ks_cnt, E.sms);
     if (L.ks_splits > 1) {
       ks_part_max = std::max(ks_part_max, (size_t)L.ks_cnt * L.ks_splits);
@@ -584,22 +634,39 @@ int plan_build(Engine &E, const arx_netlist *nl, int keyset, int mode, std::uniq
   return ARX_OK;
 }
 
+// The blind-rotation launches of a level: one, or the bulk and the tail of a
+// split (the tail's jobs and outputs follow the bulk's).  *launches counts them.
+int launch_level_br(Engine &E, const Plan &P, const Level &L, const Keyset &ks, cudaStream_t st,
+                     uint32_t *launches) {
+  if (!L.br_cnt) return ARX_OK;
+  const int first = L.br_split ? L.br_split : L.br_cnt;
+  BrArgs a{};
+  a.bsk[0] = ks.bsk;
+  a.wires = P.wires.as<uint32_t>();
+  a.jobs = P.brjobs.as<BrJob>() + L.br_off;
+  a.num_jobs = first;
+  a.n = P.n;
+  a.out = P.brout.as<uint32_t>();
+  a.tg = E.tg;
+  a.status = E.status;
+  a.tc = E.tc;
+  CK(launch_br(a, L.shape, L.grid, st));
+  if (launches) ++*launches;
+  if (L.br_split) {
+    a.jobs += first;
+    a.num_jobs = L.br_cnt - first;
+    a.out += (size_t)first * kOutStride;
+    CK(launch_br(a, L.shape2, L.grid2, st));
+    if (launches) ++*launches;
+  }
+  return ARX_OK;
+}
+
 int plan_launch_levels(Engine &E, Plan &P, cudaStream_t st) {
   Keyset &ks = E.keysets[P.keyset];
   for (const Level &L : P.levels) {
-    if (L.br_cnt) {
-      BrArgs a{};
-      a.bsk[0] = ks.bsk;
-      a.wires = P.wires.as<uint32_t>();
-      a.jobs = P.brjobs.as<BrJob>() + L.br_off;
-      a.num_jobs = L.br_cnt;
-      a.n = P.n;
-      a.out = P.brout.as<uint32_t>();
-      a.tg = E.tg;
-      a.status = E.status;
-      a.tc = E.tc;
-      CK(launch_br(a, L.shape, L.grid, st));
-    }
+    const int rc = launch_level_br(E, P, L, ks, st, nullptr);
+    if (rc) return rc;
     KsArgs k{};
     k.ksk[0] = ks.ksk;
     k.br_out = P.brout.as<uint32_t>();
@@ -1016,6 +1083,26 @@ extern "C" int arx_plan_shapes(int plan, uint32_t *H, uint32_t *GT, uint32_t *jo
   return (int)P.levels.size();
 }
 
+extern "C" int arx_plan_launches(int plan, uint32_t *wave, uint32_t *H, uint32_t *GT, uint32_t *jobs, uint32_t cap) {
+  API_BEGIN
+  if (plan < 0 || plan >= (int)E.plans.size() || !E.plans[plan]) return fail(ARX_EINVAL, "no plan %d", plan);
+  const Plan &P = *E.plans[plan];
+  uint32_t k = 0;
+  for (size_t w = 0; w < P.levels.size(); ++w) {
+    const Level &L = P.levels[w];
+    if (!L.br_cnt) continue;
+    for (int part = 0; part < (L.br_split ? 2 : 1); ++part, ++k) {
+      if (k >= cap) continue;
+      const BrShape s = part ? L.shape2 : L.shape;
+      if (wave) wave[k] = (uint32_t)w;
+      if (H) H[k] = (uint32_t)s.H;
+      if (GT) GT[k] = (uint32_t)s.GT;
+      if (jobs) jobs[k] = (uint32_t)(L.br_split ? (part ? L.br_cnt - L.br_split : L.br_split) : L.br_cnt);
+    }
+  }
+  return (int)k;
+}
+
 extern "C" int arx_plan_wires(int plan, const uint32_t *ids, size_t count, uint32_t *out) {
   API_BEGIN
   if (plan < 0 || plan >= (int)E.plans.size() || !E.plans[plan]) return fail(ARX_EINVAL, "no plan %d", plan);
@@ -1060,20 +1147,8 @@ extern "C" int arx_plan_profile(int plan, const uint32_t *ct_in, float *br_ms, f
   for (size_t l = 0; l < P.levels.size(); ++l) {
     const Level &L = P.levels[l];
     CK(cudaEventRecord(ev[4 * l], st));
-    if (L.br_cnt) {
-      BrArgs a{};
-      a.bsk[0] = ks->bsk;
-      a.wires = P.wires.as<uint32_t>();
-      a.jobs = P.brjobs.as<BrJob>() + L.br_off;
-      a.num_jobs = L.br_cnt;
-      a.n = P.n;
-      a.out = P.brout.as<uint32_t>();
-      a.tg = E.tg;
-      a.status = E.status;
-      a.tc = E.tc;
-      CK(launch_br(a, L.shape, L.grid, st));
-      ++nb;
-    }
+    rc = launch_level_br(E, P, L, *ks, st, &nb);
+    if (rc) return rc;
     CK(cudaEventRecord(ev[4 * l + 1], st));
     CK(cudaEventRecord(ev[4 * l + 2], st));
     KsArgs k{};

@@ -43,6 +43,11 @@ struct Level {
   int br_off = 0, br_cnt = 0, ks_off = 0, ks_cnt = 0;
   BrShape shape{1, 1};
   int grid = 1;
+  // a level split over two blind-rotation launches: the first br_split jobs on
+  // `shape`, the rest on shape2 (br_split = 0: one launch of all br_cnt)
+  int br_split = 0;
+  BrShape shape2{0, 0};
+  int grid2 = 0;
   int ks_splits = 1;
 };
 
@@ -77,10 +82,19 @@ struct ShapePolicy {
   BrShape heuristic(int jobs) const;
   BrShape wide(int jobs) const;  // the throughput shapes of the heuristic
   BrShape pick(int jobs, int n) const;
-  // The most blind rotations one launch takes at the cost of a launch of `jobs`
+  // Autotuned cost (ms per CMux) of `jobs` blind rotations as one launch of the
+  // best shape (the one pick takes, stored in *s).
+  double launch_cost(int jobs, BrShape *s) const;
+  // The cheapest way, by the autotuned table, to run `jobs` blind rotations as at
+  // most two launches: rounds of one throughput shape (*bulk, the first
+  // *bulk_jobs) and the rest on the best shape for them (*tail; {0, 0} when one
+  // launch is cheapest).  Returns its cost (ms per CMux).
+  double split(int jobs, BrShape *bulk, int *bulk_jobs, BrShape *tail) const;
+  // The most blind rotations one level takes at the cost of a level of `jobs`
   // (gadget length l): a cluster kernel's wave costs the same for every count up
   // to its co-resident clusters, so the rest of that width is free; with the
-  // autotuned table the costs are the measured ones.
+  // autotuned table the costs are the measured ones, of the level's launches as
+  // split chooses them.
   int free_capacity(int jobs, int n, int l) const;
   // Key sets with gadget l = 2 (given the shape chosen for l = 3 and the wave's
   // blind rotations): their own sixteen-CTA kernel while the wave's gates fit

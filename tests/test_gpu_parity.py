@@ -332,6 +332,33 @@ def test_graph_mode_equals_plain_mode(O, keys630, gpu630):
     assert np.array_equal(arx.client_decrypt(630, keys630.s, a), nl.plain_eval(bits))
 
 
+def test_split_wave_bulk_and_tail_launches(O, keys630, gpu630):
+    """One wave of six full rounds of 152 SMs' tiles plus 8 gates: the autotuned
+    plan runs the rounds on the throughput kernel and the 8 left over as a second
+    launch on a shape sized for them; every output equals plain mode's, and
+    sampled gates from both launches (the tail is the wave's last jobs) equal the
+    oracle's."""
+    g = 6 * arx.device_sms() + 8
+    types = I.random_gate_types(17, g)
+    nl = I.Netlist(2 * g, types, np.arange(g, dtype=np.uint32), np.arange(g, 2 * g, dtype=np.uint32),
+                   np.zeros(g, np.uint32), np.arange(2 * g, 3 * g, dtype=np.uint32), "gates%d" % g)
+    bits, ct = _encrypt_inputs(O, keys630, nl, 97)
+    plain = np.zeros((g, 631), np.uint32)
+    arx.eval_netlist_ex(nl, ct, plain, mode=arx.MODE_PLAIN)
+    out = np.zeros_like(plain)
+    with arx.Plan(nl, mode=arx.MODE_GRAPH) as p:
+        ls = p.launches()
+        assert p.waves == 1 and sum(j for _, _, _, j in ls) == g
+        assert len(ls) == 2 and ls[1][3] == 8, ls
+        p.run(ct, out)
+    assert np.array_equal(out, plain)
+    assert np.array_equal(arx.client_decrypt(630, keys630.s, out), nl.plain_eval(bits))
+    pick = np.array(sorted(set(list(np.random.default_rng(9).choice(g - 8, 8, replace=False)) +
+                               list(range(g - 10, g)))))
+    want = keys630.ctx.gates(types[pick], ct[pick], ct[g + pick])
+    assert np.array_equal(out[pick], want)
+
+
 def test_graph_plan_balances_launch_widths(O, keys630, gpu630):
     """Graph plans place gates within their slack: config 2's 128-wide first wave
     and its 8- to 15-gate waves are spread so that at most one launch exceeds the
