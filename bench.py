@@ -71,12 +71,12 @@ ALU_PEAK_TMODMUL = 152 * 2.070e9 * 64 / 3 / 1e12
 # build (profiles/): the key once per launch.  Only kernels listed here report it.
 TRAFFIC_PER_LAUNCH = {
     "br_cluster16_kernel": 62.06e6 + 2.46e6,  # 7 gates
-    "br_cluster16_kernel<L=2>": 33.65e6 + 0.002e6,  # 7 gates, n = 512, l = 2
+    "br_cluster16_kernel<L=2>": 33.66e6 + 0.0e6,  # 7 gates, n = 512, l = 2
     "br_cluster8_kernel": 62.06e6 + 2.08e6,   # 8 gates
     "br_kernel<1,6>": 66.89e6 + 2.69e6,       # 912 gates
-    "br_kernel<1,6,L=2>": 37.65e6 + 0.06e6,   # 912 gates, n = 512, l = 2
+    "br_kernel<1,6,L=2>": 37.64e6 + 0.09e6,   # 912 gates, n = 512, l = 2
     "br_cluster8_kernel<L=2>": 33.68e6 + 6.40e6,  # 8 gates, n = 512, l = 2
-    "br_kernel<4,1,L=2>": 34.23e6 + 3.58e6,       # 128 gates, n = 512, l = 2
+    "br_kernel<4,1,L=2>": 34.26e6 + 0.001e6,      # 128 gates, n = 512, l = 2
 }
 KERNEL_OF_H = {12: "br_cluster_kernel", 24: "br_cluster4_kernel", 48: "br_cluster8_kernel",
                40: "br_cluster8_kernel<L=2>", 80: "br_cluster16_kernel<L=2>", 96: "br_cluster16_kernel"}
