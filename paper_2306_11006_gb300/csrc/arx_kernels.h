@@ -12,6 +12,7 @@ constexpr int kMaxLweN = 630;     // largest LWE dimension the device layouts ho
 constexpr int kWireStride = 632;  // words per LWE_n ciphertext in device buffers
 constexpr int kOutStride = 1028;  // words per extracted LWE_N sample
 constexpr int kKsRowStride = 632; // words per key-switching-key row
+constexpr int kKsZeroWords = 640; // zero words after the key-switching-key rows (read for digit 0)
 constexpr int kChunkWords = 2 * 2 * kN;       // one BSK row: [c_out 2][prime 2][N]
 constexpr int kChunkBytes = kChunkWords * 4;  // 16 KiB
 constexpr uint32_t kQ0 = 134215681u;  // CRT primes: = 1 mod 2048, 32 q < 2^32

@@ -820,7 +820,7 @@ int bootstrap_gates(Engine &E, const uint8_t *types, const uint32_t *a, const ui
 // keys
 // --------------------------------------------------------------------------
 size_t keyset_bytes(int n, int l) {
-  return (size_t)n * 2 * l * kChunkBytes + (size_t)kN * 8 * 3 * kKsRowStride * 4;
+  return (size_t)n * 2 * l * kChunkBytes + ((size_t)kN * 8 * 3 * kKsRowStride + kKsZeroWords) * 4;
 }
 
 int load_keys(Engine &E, const uint32_t *bsk, const uint32_t *ksk, int n, int l, cudaStream_t user_st) {
@@ -835,7 +835,7 @@ int load_keys(Engine &E, const uint32_t *bsk, const uint32_t *ksk, int n, int l,
   K.l = l;
   const int rows = 2 * l;
   const size_t bsk_ntt = (size_t)n * rows * kChunkBytes;
-  const size_t ksk_dev = (size_t)kN * 8 * 3 * kKsRowStride * 4;
+  const size_t ksk_dev = ((size_t)kN * 8 * 3 * kKsRowStride + kKsZeroWords) * 4;  // + the zero row
   const size_t bsk_coef = (size_t)n * rows * 2 * kN * 4;
   cudaError_t e = cudaMalloc(&K.bsk, bsk_ntt);
   if (e == cudaSuccess) e = cudaMalloc(&K.ksk, ksk_dev);

@@ -148,7 +148,7 @@ def test_client_encrypt_decrypt_match_oracle(O):
 
 
 def test_keyset_bytes():
-    assert arx.keyset_bytes(630) == 630 * 6 * 16384 + 1024 * 8 * 3 * 632 * 4
+    assert arx.keyset_bytes(630) == 630 * 6 * 16384 + (1024 * 8 * 3 * 632 + 640) * 4  # + the zero row
     assert arx.keyset_bytes(0) == 0
 
 
