@@ -265,13 +265,13 @@ def single_core_rate(O, ctx, nl, wires, n: int, gates: int = 8):
             "sample": f"the netlist's first {len(g)} bootstrapped gates on one thread, {dt:.1f} s"}
 
 
-def oracle_leg(nl, n: int, l: int, gpu_wires=None, sample_gates: int = 48):
+def oracle_leg(nl, n: int, l: int, gpu_wires=None, sample_gates: int = 48, gates=None):
     """The plain C oracle on this host's cores.  Small netlists (config 2) are
     evaluated in full with every wire kept, timed, and -- given gpu_wires(ids), a
     reader of the GPU run's wires -- compared bit for bit, every wire.  Large
-    netlists are sampled: `sample_gates` gates drawn from the netlist, each
-    evaluated by the oracle on the GPU run's input wires and compared with the
-    GPU's output wire (and timed)."""
+    netlists are sampled: the given `gates` (else `sample_gates` gates drawn from
+    the netlist), each evaluated by the oracle on the GPU run's input wires and
+    compared with the GPU's output wire (and timed)."""
     cores = os.cpu_count() or 1
     O, kr, ctx, bits, ct_in = oracle_inputs(nl, n, l)
     boots_total = nl.num_bootstraps
@@ -298,6 +298,8 @@ def oracle_leg(nl, n: int, l: int, gpu_wires=None, sample_gates: int = 48):
     rng = np.random.default_rng(11)
     boot_gates = np.array([k for k in range(nl.num_gates) if I.BOOTSTRAPS[int(nl.type[k])]], np.int64)
     g = np.sort(rng.choice(boot_gates, size=min(sample_gates, len(boot_gates)), replace=False))
+    if gates is not None:
+        g = np.sort(np.asarray(gates, np.int64))
     rec_check = {"wires_compared": 0, "mismatched": None}
     if gpu_wires is None:
         return None, rec_check
@@ -306,9 +308,9 @@ def oracle_leg(nl, n: int, l: int, gpu_wires=None, sample_gates: int = 48):
     got = ctx.gates(np.asarray(nl.type)[g].astype(np.uint8), a, b, c, nthreads=cores)
     dt = time.perf_counter() - t0
     boots = int(sum(I.BOOTSTRAPS[int(t)] for t in np.asarray(nl.type)[g]))
+    what = "gates given" if gates is not None else "gates drawn from the netlist"
     rec.update({"value": boots / dt, "seconds": dt,
-                "sample": f"{len(g)} gates drawn from the netlist, each on the GPU run's input wires, "
-                          f"{dt:.1f} s on {cores} threads"})
+                "sample": f"{len(g)} {what}, each on the GPU run's input wires, {dt:.1f} s on {cores} threads"})
     bad = int(np.count_nonzero(np.any(got != gpu_wires((nl.num_inputs + g).astype(np.uint32)), axis=1)))
     return rec, {"wires_compared": int(len(g)), "mismatched": bad}
 
@@ -672,6 +674,17 @@ def main():
         dag, ddesc = workload("dag")
         brec, bplan = measure_plan(arx, torch, dag, ddesc + " (batched: one CUDA graph, autotuned shapes)", args,
                                    n, l, keyset, kr, dev, stream, 3, 1, arx.MODE_GRAPH, e2e=False)
+        # every gate of three levels of the netlist's levelization (the narrowest of
+        # each third of its depth), each on the GPU run's own input wires
+        wave, depth = arx.levelize(dag)
+        widths = np.bincount(wave, minlength=depth)
+        thirds = [range(k * depth // 3, max((k + 1) * depth // 3, k * depth // 3 + 1)) for k in range(3)]
+        picked = sorted({min(t, key=lambda L: widths[L]) for t in thirds})
+        gates = np.nonzero(np.isin(wave, picked))[0]
+        _, bcheck = oracle_leg(dag, n, l, lambda ids: bplan.wires(ids, n), gates=gates)
+        bcheck["levels"] = [int(L) for L in picked]
+        brec["oracle_check"] = bcheck
+        brec["verified"] = bool(brec["verified"] and bcheck["mismatched"] == 0)
         bplan.close()
         line["batched"] = brec
     arx.unload_keys(keyset)
