@@ -171,6 +171,20 @@ int arx_levelize(const arx_netlist *nl, uint32_t *wave, uint32_t *depth);
 int arx_levelize_balanced(const arx_netlist *nl, const uint32_t *caps, uint32_t ncaps, uint32_t *wave,
                           uint32_t *depth);
 
+/* The launch plan of one wave under a table of launch shapes (host only; what
+ * graph plans compute from the autotuner's measured table).  Shape s costs
+ * ms[s] per round of up to gates[s] blind rotations (a persistent launch pays
+ * whole rounds); cluster[s] != 0 marks a shape that takes no bulk rounds of a
+ * split.  For `jobs` blind rotations: the cheapest of one launch and of two --
+ * k rounds of a non-cluster shape, the rest on the best shape for them -- as
+ * *bulk (shape index) for the first *bulk_jobs and *tail (shape index, -1: one
+ * launch) for the rest, *cost (ms), and *cap: the widest wave that one or two
+ * such launches run within *cost (graph plans fill a level up to it).  Host
+ * arrays of `shapes` entries (1..64; ms > 0, gates > 0); outputs may be NULL.
+ * ARX_EINVAL on bad arguments.  No counterpart in the paper: scheduling. */
+int arx_split_wave(const double *ms, const uint32_t *gates, const uint8_t *cluster, uint32_t shapes, uint32_t jobs,
+                   uint32_t *bulk, uint32_t *bulk_jobs, int32_t *tail, double *cost, uint32_t *cap);
+
 /* Evaluate a netlist with the default key set (Sec. 4.2): the gates are
  * levelized into waves (arx_levelize), and every wave -- all of its ready gates,
  * of any types -- runs as one blind-rotation launch and one key-switch launch,

@@ -63,6 +63,7 @@ SIGNATURES = {
     "arx_plan_info": (_i, [_i, _vp, _vp, _vp]),
     "arx_plan_shapes": (_i, [_i, _vp, _vp, _vp, _u32]),
     "arx_plan_launches": (_i, [_i, _vp, _vp, _vp, _vp, _u32]),
+    "arx_split_wave": (_i, [_vp, _vp, _vp, _u32, _u32, _vp, _vp, _vp, _vp, _vp]),
     "arx_plan_wires": (_i, [_i, _vp, _sz, _vp]),
     "arx_set_launch_shape": (_i, [_i, _i]),
     "arx_plan_profile": (_i, [_i, _vp, _vp, _vp, _vp, _vp]),
@@ -225,6 +226,22 @@ def levelize_balanced(nl, caps):
     _check(lib().arx_levelize_balanced(r.ref, _ptr(c) if len(c) else None, len(c), _ptr(wave),
                                        ctypes.addressof(depth)))
     return wave[: len(r.type)], depth.value
+
+
+def split_wave(ms, gates, cluster, jobs):
+    """Launch plan of one wave under a table of shapes (arx_split_wave): returns
+    (bulk shape, bulk jobs, tail shape or -1, cost in ms, widest wave within it)."""
+    m = np.ascontiguousarray(np.asarray(ms, dtype=np.float64))
+    g = np.ascontiguousarray(np.asarray(gates, dtype=np.uint32))
+    c = np.ascontiguousarray(np.asarray(cluster, dtype=np.uint8))
+    if not (len(m) == len(g) == len(c)):
+        raise ArxError(-1, "ms, gates and cluster differ in length")
+    bulk, bj, cap = ctypes.c_uint32(0), ctypes.c_uint32(0), ctypes.c_uint32(0)
+    tail, cost = ctypes.c_int32(0), ctypes.c_double(0)
+    _check(lib().arx_split_wave(_ptr(m), _ptr(g), _ptr(c), len(m), int(jobs), ctypes.addressof(bulk),
+                                ctypes.addressof(bj), ctypes.addressof(tail), ctypes.addressof(cost),
+                                ctypes.addressof(cap)))
+    return bulk.value, bj.value, tail.value, cost.value, cap.value
 
 
 def eval_netlist(nl, ct_in, ct_out) -> None:

@@ -1011,6 +1011,32 @@ extern "C" int arx_levelize_balanced(const arx_netlist *nl, const uint32_t *caps
   return ARX_OK;
 }
 
+extern "C" int arx_split_wave(const double *ms, const uint32_t *gates, const uint8_t *cluster, uint32_t shapes,
+                               uint32_t jobs, uint32_t *bulk, uint32_t *bulk_jobs, int32_t *tail, double *cost,
+                               uint32_t *cap) {
+  if (!ms || !gates || !cluster || shapes < 1 || shapes > 64 || jobs < 1 || jobs > (1u << 30))
+    return fail(ARX_EINVAL, "bad split arguments");
+  ShapePolicy pol;  // a table of synthetic shapes; shape s is (H, s + 1), H marking cluster shapes
+  pol.tuned_n = 1;
+  for (uint32_t s = 0; s < shapes; ++s) {
+    if (!(ms[s] > 0.0) || !gates[s]) return fail(ARX_EINVAL, "shape %u: ms and gates must be positive", s);
+    TuneEntry t;
+    t.shape = BrShape{cluster[s] ? kCluster16H : 1, (int)s + 1};
+    t.wave_ms_per_cmux = ms[s];
+    t.gates_per_wave = (int)gates[s];
+    pol.tune.push_back(t);
+  }
+  BrShape b{1, 1}, t2{0, 0};
+  int bj = 0;
+  const double c = pol.split((int)jobs, &b, &bj, &t2);
+  if (bulk) *bulk = (uint32_t)(b.GT - 1);
+  if (bulk_jobs) *bulk_jobs = (uint32_t)bj;
+  if (tail) *tail = t2.H ? t2.GT - 1 : -1;
+  if (cost) *cost = c;
+  if (cap) *cap = (uint32_t)pol.free_capacity((int)jobs, 1, 3);
+  return ARX_OK;
+}
+
 extern "C" int arx_eval_netlist_ex(const arx_netlist *nl, const uint32_t *ct_in, uint32_t *ct_out, int keyset,
                                    int mode, void *stream) {
   API_BEGIN
