@@ -84,30 +84,37 @@ constexpr int kKsThreads = 160;             // 160 x 4 words >= 632
 constexpr int kKsVec = kKsRowStride / 4;    // 158 uint4 per row
 
 // acc -= the key rows selected by the base-4 digits of positions [i0, i1) of lwe
-// (each rounded to 16 bits), columns 4 t .. 4 t + 3.  Digit 0 reads the zero
-// row after the key rows, so that every load is unconditional and the 16 of an
-// iteration are in flight together (threads t >= kKsVec read in bounds and
-// discard what they read): 64 -> 84 registers a thread, headline step 67.5 ->
-// 67.2 ms.
-__device__ __forceinline__ void ks_accumulate(uint4 &acc, const uint4 *__restrict__ ksk, const uint32_t *lwe, int i0,
-                                              int i1, int t) {
-  constexpr int kPos = 2;  // positions per iteration (kN / S >= 16)
-  const uint4 *zero = ksk + (size_t)kN * 8 * 3 * kKsVec;
+// (each rounded to 16 bits), columns 4 t .. 4 t + 3.  The CTA first writes the
+// row of every (position, digit) pair into roff (uint4 offsets; digit 0: the
+// zero row after the key rows, so that every load is unconditional): the digit
+// and address arithmetic is done once per CTA instead of once per thread, and
+// the loop is a broadcast shared-memory read, one load and four subtractions per
+// row, 16 rows in flight (threads t >= kKsVec read in bounds and discard what
+// they read).
+__device__ __forceinline__ void ks_accumulate(uint4 &acc, const uint4 *__restrict__ ksk, const uint32_t *lwe,
+                                              uint32_t *roff, int i0, int i1, int t) {
+  const int cnt = (i1 - i0) * 8;  // a multiple of 16 (kN / S >= 16)
+  for (int e = t; e < cnt; e += kKsThreads) {
+    const int i = i0 + (e >> 3), j = (e & 7) + 1;
+    const uint32_t y = lwe[i] + (1u << 15);  // round to 16 bits
+    const uint32_t v = (y >> (32 - 2 * j)) & 3u;
+    roff[e] = v ? (uint32_t)(((i * 8 + (j - 1)) * 3 + (int)(v - 1)) * kKsVec) : (uint32_t)(kN * 8 * 3 * kKsVec);
+  }
+  __syncthreads();
+  const uint4 *kt = ksk + t;
 #pragma unroll 1
-  for (int i = i0; i < i1; i += kPos) {
-    uint4 r[8 * kPos];
+  for (int e = 0; e < cnt; e += 16) {
+    uint4 r[16];
 #pragma unroll
-    for (int u = 0; u < kPos; ++u) {
-      const uint32_t y = lwe[i + u] + (1u << 15);  // round to 16 bits
-#pragma unroll
-      for (int j = 1; j <= 8; ++j) {
-        const uint32_t v = (y >> (32 - 2 * j)) & 3u;
-        const size_t row = ((size_t)((i + u) * 8 + (j - 1)) * 3 + (v ? v - 1 : 0)) * kKsVec;
-        r[u * 8 + j - 1] = __ldg((v ? ksk + row : zero) + t);
-      }
+    for (int q4 = 0; q4 < 4; ++q4) {
+      const uint4 o = reinterpret_cast<const uint4 *>(roff + e)[q4];
+      r[4 * q4 + 0] = __ldg(kt + o.x);
+      r[4 * q4 + 1] = __ldg(kt + o.y);
+      r[4 * q4 + 2] = __ldg(kt + o.z);
+      r[4 * q4 + 3] = __ldg(kt + o.w);
     }
 #pragma unroll
-    for (int q = 0; q < 8 * kPos; ++q) {
+    for (int q = 0; q < 16; ++q) {
       acc.x -= r[q].x;
       acc.y -= r[q].y;
       acc.z -= r[q].z;
@@ -118,6 +125,7 @@ __device__ __forceinline__ void ks_accumulate(uint4 &acc, const uint4 *__restric
 
 __global__ void __launch_bounds__(kKsThreads, 4) ks_kernel(const __grid_constant__ KsArgs args) {
   __shared__ uint32_t lwe[kN + 1];
+  __shared__ __align__(16) uint32_t roff[kN * 8];  // key row of each (position, digit) pair of this CTA
   __shared__ int last;
   const int S = args.splits;
   const int gate = blockIdx.x / S, split = blockIdx.x - gate * S;
@@ -150,7 +158,7 @@ __global__ void __launch_bounds__(kKsThreads, 4) ks_kernel(const __grid_constant
     if (n == 4 * t) acc.x = b; else if (n == 4 * t + 1) acc.y = b; else if (n == 4 * t + 2) acc.z = b; else acc.w = b;
   }
   const bool live = t < kKsVec;
-  ks_accumulate(acc, reinterpret_cast<const uint4 *>(args.ksk[jb.key]), lwe, i0, i1, t);
+  ks_accumulate(acc, reinterpret_cast<const uint4 *>(args.ksk[jb.key]), lwe, roff, i0, i1, t);
   if (S == 1) {
     if (live) {
       if (4 * t + 0 <= n) dst[4 * t + 0] = acc.x;
