@@ -83,6 +83,14 @@ __device__ __forceinline__ uint32_t mont_mul(uint32_t a, uint32_t b, const Prime
   return (uint32_t)((t + (uint64_t)m * pr.q) >> 32);
 }
 
+// Montgomery reduction of an exact sum of products: T 2^-32 mod q, below
+// T / 2^32 + q, for T < 2^63 (the sum of up to six products x b with x < 22q,
+// b < q is below 132 q^2 < 2^62, reduced below 5.2q).
+__device__ __forceinline__ uint32_t mont_redc(uint64_t t, const PrimeRT &pr) {
+  const uint32_t m = (uint32_t)t * pr.qni;
+  return (uint32_t)((t + (uint64_t)m * pr.q) >> 32);
+}
+
 __device__ __forceinline__ uint32_t csub(uint32_t x, uint32_t m) { return min(x, x - m); }
 
 __device__ __forceinline__ void ct_bfly(uint32_t &x, uint32_t &y, uint2 z, const PrimeRT &pr) {

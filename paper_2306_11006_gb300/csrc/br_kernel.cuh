@@ -12,7 +12,9 @@
 // (cp.async.bulk into a 4..8-stage mbarrier ring) and read by all 2 GT warps that
 // use it.  There is no producer warp: the last of those warps to finish with a
 // slot refills it with the row kStages ahead, so a CTA of 12 warps keeps three
-// warps per scheduler and 168 registers a thread.  Every wait is bounded: on a
+// warps per scheduler and 168 registers a thread; CTAs of at most 8 warps have
+// the registers to keep each coefficient's MAC as an exact 64-bit sum, reduced
+// once per CMux.  Every wait is bounded: on a
 // timeout the kernel records kDevTimeout in the device status word, stops
 // waiting, runs to the end, lets its copies in flight land and returns.
 #pragma once
@@ -252,6 +254,9 @@ __device__ __forceinline__ void br_consumer(const BrShared &S, const BrArgs &arg
   constexpr int kScr = scratch_words<H>();
   constexpr int kGateThreads = 64 * H;
   constexpr int kStages = br_stages<H, GT, L>();
+  // exact 64-bit MAC sums where the CTA's warps leave a thread the registers
+  // for them (at most 8 warps: up to 255 registers a thread)
+  constexpr bool kWide = 2 * H * GT <= 8;
   const int n = args.n;
   const int bar_id = 1 + g;
   const int role = h * 2 + P;
@@ -298,8 +303,17 @@ __device__ __forceinline__ void br_consumer(const BrShared &S, const BrArgs &arg
       make_digits<kGateThreads, L>(D, A, abar[i], tid_g);
       named_bar(bar_id, kGateThreads);  // B0: digits ready
       uint32_t acc0[32], acc1[32];
+      // kWide: the MAC keeps the exact 64-bit sum of the row products (one
+      // IMAD.WIDE per product) and reduces it once after the rows
+      uint64_t wacc0[kWide ? 32 : 1], wacc1[kWide ? 32 : 1];
 #pragma unroll
-      for (int e = 0; e < 32; ++e) acc0[e] = acc1[e] = 0;
+      for (int e = 0; e < 32; ++e) {
+        if constexpr (kWide) {
+          wacc0[e] = wacc1[e] = 0;
+        } else {
+          acc0[e] = acc1[e] = 0;
+        }
+      }
 #pragma unroll 1
       for (int rr = 0; rr < kRpg; ++rr) {
         const int r = h * kRpg + rr;
@@ -322,18 +336,34 @@ __device__ __forceinline__ void br_consumer(const BrShared &S, const BrArgs &arg
         mbar_wait(S.full + slot, (jc / kStages) & 1u, S.abort_flag, args.status);
         const uint4 *B0 = reinterpret_cast<const uint4 *>(S.ring + slot * kChunkWords + (cA * 2 + P) * kN);
         const uint4 *B1 = reinterpret_cast<const uint4 *>(S.ring + slot * kChunkWords + ((1 - cA) * 2 + P) * kN);
+        if constexpr (kWide) {
 #pragma unroll
-        for (int e4 = 0; e4 < 8; ++e4) {
-          const uint4 b0 = B0[e4 * 32 + lane];
-          const uint4 b1 = B1[e4 * 32 + lane];
-          acc0[4 * e4 + 0] += mont_mul(x[4 * e4 + 0], b0.x, pr);
-          acc0[4 * e4 + 1] += mont_mul(x[4 * e4 + 1], b0.y, pr);
-          acc0[4 * e4 + 2] += mont_mul(x[4 * e4 + 2], b0.z, pr);
-          acc0[4 * e4 + 3] += mont_mul(x[4 * e4 + 3], b0.w, pr);
-          acc1[4 * e4 + 0] += mont_mul(x[4 * e4 + 0], b1.x, pr);
-          acc1[4 * e4 + 1] += mont_mul(x[4 * e4 + 1], b1.y, pr);
-          acc1[4 * e4 + 2] += mont_mul(x[4 * e4 + 2], b1.z, pr);
-          acc1[4 * e4 + 3] += mont_mul(x[4 * e4 + 3], b1.w, pr);
+          for (int e4 = 0; e4 < 8; ++e4) {
+            const uint4 b0 = B0[e4 * 32 + lane];
+            const uint4 b1 = B1[e4 * 32 + lane];
+            wacc0[4 * e4 + 0] += (uint64_t)x[4 * e4 + 0] * b0.x;
+            wacc0[4 * e4 + 1] += (uint64_t)x[4 * e4 + 1] * b0.y;
+            wacc0[4 * e4 + 2] += (uint64_t)x[4 * e4 + 2] * b0.z;
+            wacc0[4 * e4 + 3] += (uint64_t)x[4 * e4 + 3] * b0.w;
+            wacc1[4 * e4 + 0] += (uint64_t)x[4 * e4 + 0] * b1.x;
+            wacc1[4 * e4 + 1] += (uint64_t)x[4 * e4 + 1] * b1.y;
+            wacc1[4 * e4 + 2] += (uint64_t)x[4 * e4 + 2] * b1.z;
+            wacc1[4 * e4 + 3] += (uint64_t)x[4 * e4 + 3] * b1.w;
+          }
+        } else {
+#pragma unroll
+          for (int e4 = 0; e4 < 8; ++e4) {
+            const uint4 b0 = B0[e4 * 32 + lane];
+            const uint4 b1 = B1[e4 * 32 + lane];
+            acc0[4 * e4 + 0] += mont_mul(x[4 * e4 + 0], b0.x, pr);
+            acc0[4 * e4 + 1] += mont_mul(x[4 * e4 + 1], b0.y, pr);
+            acc0[4 * e4 + 2] += mont_mul(x[4 * e4 + 2], b0.z, pr);
+            acc0[4 * e4 + 3] += mont_mul(x[4 * e4 + 3], b0.w, pr);
+            acc1[4 * e4 + 0] += mont_mul(x[4 * e4 + 0], b1.x, pr);
+            acc1[4 * e4 + 1] += mont_mul(x[4 * e4 + 1], b1.y, pr);
+            acc1[4 * e4 + 2] += mont_mul(x[4 * e4 + 2], b1.z, pr);
+            acc1[4 * e4 + 3] += mont_mul(x[4 * e4 + 3], b1.w, pr);
+          }
         }
         __syncwarp();
         if (lane == 0) {  // the slot's last user refills it
@@ -343,6 +373,13 @@ __device__ __forceinline__ void br_consumer(const BrShared &S, const BrArgs &arg
             S.cnt[slot] = 0u;
             if (jc + kStages < rows) issue_row<kStages, GT, L>(S, args, jc + kStages, it, tile_bsk);
           }
+        }
+      }
+      if constexpr (kWide) {
+#pragma unroll
+        for (int e = 0; e < 32; ++e) {
+          acc0[e] = mont_redc(wacc0[e], pr);
+          acc1[e] = mont_redc(wacc1[e], pr);
         }
       }
 
