@@ -108,6 +108,75 @@ __device__ __forceinline__ void named_bar(int id, int threads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
 }
 
+// ---- tensor memory (TMEM) as a spill space for the MAC sums ---------------
+// A warp may address only its quadrant of the 128 TMEM lanes: lanes
+// 32 (w mod 4) .. + 31 for warp w of the CTA; lane i of the warp holds TMEM lane
+// 32 (w mod 4) + i.  Address: lane << 16 | column.  Each helper waits for its
+// own access, so registers are free (store) or valid (load) on return.
+__device__ __forceinline__ void tmem_ld64(uint32_t (&r)[64], uint32_t taddr) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47, %48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63}, [%64];\n"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]),
+        "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]),
+        "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]),
+        "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]),
+        "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+      : "r"(taddr)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_st64(uint32_t taddr, const uint32_t (&r)[64]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x64.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47, %48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63, %64};\n"
+      "tcgen05.wait::st.sync.aligned;"
+      :
+      : "r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+        "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]),
+        "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]),
+        "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31]),
+        "r"(r[32]), "r"(r[33]), "r"(r[34]), "r"(r[35]), "r"(r[36]), "r"(r[37]), "r"(r[38]), "r"(r[39]),
+        "r"(r[40]), "r"(r[41]), "r"(r[42]), "r"(r[43]), "r"(r[44]), "r"(r[45]), "r"(r[46]), "r"(r[47]),
+        "r"(r[48]), "r"(r[49]), "r"(r[50]), "r"(r[51]), "r"(r[52]), "r"(r[53]), "r"(r[54]), "r"(r[55]),
+        "r"(r[56]), "r"(r[57]), "r"(r[58]), "r"(r[59]), "r"(r[60]), "r"(r[61]), "r"(r[62]), "r"(r[63])
+      : "memory");
+}
+
+// One warp allocates `cols` TMEM columns (a power of two, 32 .. 512) and gives up
+// the CTA's right to allocate more; the address lands in *dst (shared memory).
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t cols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(cols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t cols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(cols) : "memory");
+}
+
+__device__ __forceinline__ void tmem_fence_before_sync() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_fence_after_sync() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// w[2i], w[2i + 1]: low and high word of a 64-bit sum; adds x b.
+__device__ __forceinline__ void mac64(uint32_t (&w)[64], int i, uint32_t x, uint32_t b) {
+  const uint64_t t = (((uint64_t)w[2 * i + 1] << 32) | w[2 * i]) + (uint64_t)x * b;
+  w[2 * i] = (uint32_t)t;
+  w[2 * i + 1] = (uint32_t)(t >> 32);
+}
+
+__device__ __forceinline__ uint64_t pair64(const uint32_t (&w)[64], int i) {
+  return ((uint64_t)w[2 * i + 1] << 32) | w[2 * i];
+}
+
 __device__ __forceinline__ uint32_t modswitch(uint32_t x) { return (x + (1u << 20)) >> 21; }
 
 // (x0 mod q0, x1 mod q1), each in [0, 2q) -> the centred integer V, mod 2^32.
@@ -163,6 +232,7 @@ struct BrShared {
   uint32_t *cnt;      // kStages: warps done with the slot's current row
   uint32_t *issued;   // kStages: 1 + the last row copied into the slot
   volatile int *abort_flag;
+  uint32_t *tmem;     // TMEM base address written by tcgen05.alloc (tmem_mac shapes)
 };
 
 constexpr int kAbarPitch = 640;
@@ -213,8 +283,22 @@ __device__ __forceinline__ BrShared br_carve(uint8_t *smem) {
   s.cnt = reinterpret_cast<uint32_t *>(s.full + kStages);
   s.issued = s.cnt + kStages;
   s.abort_flag = reinterpret_cast<volatile int *>(s.issued + kStages);
+  s.tmem = reinterpret_cast<uint32_t *>(s.issued + kStages + 1);
   return s;
 }
+
+// MAC forms.  wide_mac: CTAs of at most 8 warps (a thread may hold 255
+// registers) keep each coefficient's exact 64-bit sum of row products in
+// registers.  tmem_mac: the 12-warp shapes whose warps take at least two rows
+// (168 registers a thread) keep those sums in tensor memory between rows, 128
+// columns per warp (three warps share each lane quadrant: 384 of the 512
+// columns allocated).  Both reduce once per CMux.  Otherwise (one row per warp)
+// each product is reduced on its own.
+template <int H, int GT, int L>
+__host__ __device__ constexpr bool wide_mac() { return 2 * H * GT <= 8; }
+template <int H, int GT, int L>
+__host__ __device__ constexpr bool tmem_mac() { return !wide_mac<H, GT, L>() && 2 * L / H >= 2; }
+constexpr uint32_t kTmemCols = 512;
 
 // Key rows this CTA consumes: 2L n per tile of GT gates (2L TGSW rows per CMux).
 template <int GT, int L>
@@ -247,16 +331,16 @@ __device__ __forceinline__ void issue_row(const BrShared &S, const BrArgs &args,
 // same code serves both primes; the owner of output c (warp (P, c) for H > 1,
 // both outputs for H = 1) keeps that output's accumulator in acc0.
 template <int H, int GT, int L>
-__device__ __forceinline__ void br_consumer(const BrShared &S, const BrArgs &args, int g, int h, int P, int lane) {
+__device__ __forceinline__ void br_consumer(const BrShared &S, const BrArgs &args, int g, int h, int P, int lane,
+                                            uint32_t taddr) {
   constexpr int kRows = 2 * L;  // TGSW rows per CMux
   static_assert(kRows % H == 0, "row groups");
   constexpr int kRpg = kRows / H;
   constexpr int kScr = scratch_words<H>();
   constexpr int kGateThreads = 64 * H;
   constexpr int kStages = br_stages<H, GT, L>();
-  // exact 64-bit MAC sums where the CTA's warps leave a thread the registers
-  // for them (at most 8 warps: up to 255 registers a thread)
-  constexpr bool kWide = 2 * H * GT <= 8;
+  constexpr bool kWide = wide_mac<H, GT, L>();
+  constexpr bool kTmem = tmem_mac<H, GT, L>();  // taddr: this warp's 128 TMEM columns
   const int n = args.n;
   const int bar_id = 1 + g;
   const int role = h * 2 + P;
@@ -310,7 +394,7 @@ __device__ __forceinline__ void br_consumer(const BrShared &S, const BrArgs &arg
       for (int e = 0; e < 32; ++e) {
         if constexpr (kWide) {
           wacc0[e] = wacc1[e] = 0;
-        } else {
+        } else if constexpr (!kTmem) {
           acc0[e] = acc1[e] = 0;
         }
       }
@@ -350,6 +434,30 @@ __device__ __forceinline__ void br_consumer(const BrShared &S, const BrArgs &arg
             wacc1[4 * e4 + 2] += (uint64_t)x[4 * e4 + 2] * b1.z;
             wacc1[4 * e4 + 3] += (uint64_t)x[4 * e4 + 3] * b1.w;
           }
+        } else if constexpr (kTmem) {
+          // this row's products join the exact sums kept in TMEM: output cA in
+          // columns 0 .. 63 of the warp's block, 1 - cA in 64 .. 127
+#pragma unroll 1
+          for (int o = 0; o < 2; ++o) {
+            const uint4 *B = o == 0 ? B0 : B1;
+            uint32_t w[64];
+            __syncwarp();
+            if (rr == 0) {
+#pragma unroll
+              for (int k = 0; k < 64; ++k) w[k] = 0u;
+            } else {
+              tmem_ld64(w, taddr + 64u * (uint32_t)o);
+            }
+#pragma unroll
+            for (int e4 = 0; e4 < 8; ++e4) {
+              const uint4 b = B[e4 * 32 + lane];
+              mac64(w, 4 * e4 + 0, x[4 * e4 + 0], b.x);
+              mac64(w, 4 * e4 + 1, x[4 * e4 + 1], b.y);
+              mac64(w, 4 * e4 + 2, x[4 * e4 + 2], b.z);
+              mac64(w, 4 * e4 + 3, x[4 * e4 + 3], b.w);
+            }
+            tmem_st64(taddr + 64u * (uint32_t)o, w);
+          }
         } else {
 #pragma unroll
           for (int e4 = 0; e4 < 8; ++e4) {
@@ -381,6 +489,16 @@ __device__ __forceinline__ void br_consumer(const BrShared &S, const BrArgs &arg
           acc0[e] = mont_redc(wacc0[e], pr);
           acc1[e] = mont_redc(wacc1[e], pr);
         }
+      }
+      if constexpr (kTmem) {
+        uint32_t w[64];
+        __syncwarp();
+        tmem_ld64(w, taddr);
+#pragma unroll
+        for (int e = 0; e < 32; ++e) acc0[e] = mont_redc(pair64(w, e), pr);
+        tmem_ld64(w, taddr + 64u);
+#pragma unroll
+        for (int e = 0; e < 32; ++e) acc1[e] = mont_redc(pair64(w, e), pr);
       }
 
       // prime P combines coefficients e in [16 P, 16 P + 16) and sends the other half;
@@ -493,13 +611,32 @@ __global__ void __launch_bounds__(2 * H * GT * 32, 1) br_kernel(const __grid_con
   __syncthreads();
   if (threadIdx.x == 0) stamp_start(args.stamps);
   if (args.num_jobs <= 0) return;
+  constexpr bool kTmem = tmem_mac<H, GT, L>();
+  static_assert(!kTmem || 2 * H * GT == 12, "TMEM columns: three warps per lane quadrant, 128 columns each");
+  uint32_t tbase = 0;
+  if constexpr (kTmem) {  // freed below on every path that reaches this point
+    if (warp == 0) tmem_alloc(S.tmem, kTmemCols);
+    tmem_fence_before_sync();
+    __syncthreads();
+    tmem_fence_after_sync();
+    tbase = *S.tmem;
+  }
   if (threadIdx.x == 0) {  // the first kStages rows; later ones are issued by the warps
     const uint32_t rows = cta_rows<GT, L>(args);
     for (uint32_t jc = 0; jc < (uint32_t)kStages && jc < rows; ++jc) issue_row<kStages, GT, L>(S, args, jc);
   }
   const int g = warp / (2 * H), role = warp % (2 * H);
-  br_consumer<H, GT, L>(S, args, g, role >> 1, role & 1, lane);
+  // warp w: TMEM lanes 32 (w mod 4) .. + 31, columns 128 (w / 4) .. + 127
+  const uint32_t taddr = tbase + ((32u * (uint32_t)(warp & 3)) << 16) + 128u * (uint32_t)(warp >> 2);
+  br_consumer<H, GT, L>(S, args, g, role >> 1, role & 1, lane, taddr);
+  if constexpr (kTmem) tmem_fence_before_sync();
   __syncthreads();
+  if constexpr (kTmem) {
+    if (warp == 0) {
+      tmem_fence_after_sync();
+      tmem_dealloc(tbase, kTmemCols);
+    }
+  }
   if (threadIdx.x == 0 && *S.abort_flag) {  // after a timeout: let copies in flight land (bounded)
     for (int s = 0; s < kStages; ++s) {
       const uint32_t k = S.issued[s];
