@@ -200,25 +200,35 @@ __device__ __forceinline__ uint32_t crt_torus(uint32_t x0, uint32_t x1) {
 }
 
 // Gadget digits of temp = X^a ACC - ACC for both polynomials, computed by the
-// gate's threads into dig[c][k]: for L = 3 three biased 7-bit fields (digit +
-// 64) with p = 1 in the low byte; for L = 2 two biased 10-bit fields (digit +
-// 512) with p = 1 in the low half.
+// gate's threads into dig[c]: for L = 3 three biased 7-bit fields (digit + 64)
+// with p = 1 in the low byte; for L = 2 two biased 10-bit fields (digit + 512)
+// with p = 1 in the low half.  Position k = r + 32 e (r = k mod 32) sits in row
+// r, 16-byte chunk (e / 4) XOR (r mod 8), word e mod 4 of a 32 x 32 word block:
+// lane r of a warp reads its positions r + 32 e as eight 16-byte loads, and a
+// thread stores the four positions of one chunk as one 16-byte store (both
+// free of bank conflicts).
 template <int kGateThreads, int L>
 __device__ __forceinline__ void make_digits(uint32_t *dig, const uint32_t *A, uint32_t a, int tid_g) {
-#pragma unroll 4
-  for (int idx = tid_g; idx < 2 * kN; idx += kGateThreads) {
-    const uint32_t c = (uint32_t)idx >> 10, k = (uint32_t)idx & 1023u;
+#pragma unroll 1
+  for (int it = tid_g; it < 2 * 256; it += kGateThreads) {  // (c, chunk j, row r)
+    const uint32_t r = (uint32_t)it & 31u, j = ((uint32_t)it >> 5) & 7u, c = (uint32_t)it >> 8;
     const uint32_t *P = A + c * kN;
-    const uint32_t j = (k - a) & 2047u;
-    uint32_t v = P[j & 1023u];
-    v = (j & 1024u) ? 0u - v : v;
-    if constexpr (L == 3) {
-      const uint32_t y = v - P[k] + kDecOffset;
-      dig[idx] = (y >> 25) | ((y >> 10) & 0x7F00u) | ((y << 5) & 0x7F0000u);
-    } else {
-      const uint32_t y = v - P[k] + kDecOffset2;
-      dig[idx] = (y >> 22) | (((y >> 12) & 0x3FFu) << 16);
+    uint32_t w[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const uint32_t k = r + 32u * (4u * j + (uint32_t)i);
+      const uint32_t jr = (k - a) & 2047u;
+      uint32_t v = P[jr & 1023u];
+      v = (jr & 1024u) ? 0u - v : v;
+      if constexpr (L == 3) {
+        const uint32_t y = v - P[k] + kDecOffset;
+        w[i] = (y >> 25) | ((y >> 10) & 0x7F00u) | ((y << 5) & 0x7F0000u);
+      } else {
+        const uint32_t y = v - P[k] + kDecOffset2;
+        w[i] = (y >> 22) | (((y >> 12) & 0x3FFu) << 16);
+      }
     }
+    reinterpret_cast<uint4 *>(dig + c * kN)[r * 8u + (j ^ (r & 7u))] = make_uint4(w[0], w[1], w[2], w[3]);
   }
 }
 
@@ -403,16 +413,25 @@ __device__ __forceinline__ void br_consumer(const BrShared &S, const BrArgs &arg
       for (int rr = 0; rr < kRpg; ++rr) {
         const int r = h * kRpg + rr;
         const int c = r / L, p = r - L * (r / L);
-        const uint32_t *dc = D + c * kN;
+        // positions lane + 32 e, e = 4 q .. 4 q + 3, from chunk q of row lane (make_digits)
+        const uint4 *dc = reinterpret_cast<const uint4 *>(D + c * kN) + lane * 8;
         uint32_t x[32];
-        if constexpr (L == 3) {
-          const uint32_t sel = 0x4440u | (uint32_t)p;  // byte p of the packed digits, zero-extended
 #pragma unroll
-          for (int e = 0; e < 32; ++e) x[e] = __byte_perm(dc[lane + 32 * e], 0u, sel);
-        } else {
-          const uint32_t sh = 16u * (uint32_t)p;  // half p of the packed digits
-#pragma unroll
-          for (int e = 0; e < 32; ++e) x[e] = (dc[lane + 32 * e] >> sh) & 0xFFFFu;
+        for (int q = 0; q < 8; ++q) {
+          const uint4 v = dc[q ^ (lane & 7)];
+          if constexpr (L == 3) {
+            const uint32_t sel = 0x4440u | (uint32_t)p;  // byte p of the packed digits, zero-extended
+            x[4 * q + 0] = __byte_perm(v.x, 0u, sel);
+            x[4 * q + 1] = __byte_perm(v.y, 0u, sel);
+            x[4 * q + 2] = __byte_perm(v.z, 0u, sel);
+            x[4 * q + 3] = __byte_perm(v.w, 0u, sel);
+          } else {
+            const uint32_t sh = 16u * (uint32_t)p;  // half p of the packed digits
+            x[4 * q + 0] = (v.x >> sh) & 0xFFFFu;
+            x[4 * q + 1] = (v.y >> sh) & 0xFFFFu;
+            x[4 * q + 2] = (v.z >> sh) & 0xFFFFu;
+            x[4 * q + 3] = (v.w >> sh) & 0xFFFFu;
+          }
         }
         ntt_fwd<L == 3 ? 2 : 1>(x, myscr, tw1f, tw2f, pr, lane, S.dtab + P * digit_tab_words<L>(), args.tc.dig4[P]);
         // MAC with the NTT-domain key row staged in the ring.
