@@ -12,9 +12,11 @@
 // (cp.async.bulk into a 4..8-stage mbarrier ring) and read by all 2 GT warps that
 // use it.  There is no producer warp: the last of those warps to finish with a
 // slot refills it with the row kStages ahead, so a CTA of 12 warps keeps three
-// warps per scheduler and 168 registers a thread; CTAs of at most 8 warps have
-// the registers to keep each coefficient's MAC as an exact 64-bit sum, reduced
-// once per CMux.  Every wait is bounded: on a
+// warps per scheduler and 168 registers a thread.  The MAC keeps each
+// coefficient's exact 64-bit sum of row products, reduced once per CMux: in
+// registers in CTAs of at most 8 warps (255 registers a thread), in tensor
+// memory (TMEM, tcgen05.alloc / ld / st) in the 12-warp shapes whose warps take
+// two or more rows.  Every wait is bounded: on a
 // timeout the kernel records kDevTimeout in the device status word, stops
 // waiting, runs to the end, lets its copies in flight land and returns.
 #pragma once
@@ -399,7 +401,7 @@ __device__ __forceinline__ void br_consumer(const BrShared &S, const BrArgs &arg
       named_bar(bar_id, kGateThreads);  // B0: digits ready
       uint32_t acc0[32], acc1[32];
       // kWide: the MAC keeps the exact 64-bit sum of the row products (one
-      // IMAD.WIDE per product) and reduces it once after the rows
+      // 32 x 32 -> 64-bit multiply-add per product) and reduces it once after the rows
       uint64_t wacc0[kWide ? 32 : 1], wacc1[kWide ? 32 : 1];
 #pragma unroll
       for (int e = 0; e < 32; ++e) {
