@@ -184,16 +184,19 @@ __device__ __forceinline__ void ntt_fwd(uint32_t (&x)[32], uint32_t *xbuf, const
 }
 
 // Gentleman-Sande butterfly of the merged inverse: (x, y) -> (x + y, (x - y) z),
-// both in [0, 2q).  kFirst: x, y < 12q (the sum of six Montgomery products),
-// else x, y < 2q.
-template <bool kFirst>
+// both in [0, 2q).  Inputs x, y < kIn q: 12 for the first stage after
+// per-product Montgomery MACs (six products, each below 2q), 8 after the exact
+// 64-bit MAC sums (one reduction per row group, below 7.2q in every shape that
+// uses them), 2 for every later stage.
+template <int kIn>
 __device__ __forceinline__ void gs_bfly(uint32_t &x, uint32_t &y, uint2 z, const PrimeRT &pr) {
+  static_assert(kIn == 2 || kIn == 8 || kIn == 12, "input bound");
   uint32_t s = x + y;
-  const uint32_t d = x - y + (kFirst ? 6u * pr.q2 : pr.q2);
-  if (kFirst) {
-    s = csub(s, 8u * pr.q2);  // < 24q -> < 16q
-    s = csub(s, 4u * pr.q2);
-    s = csub(s, 2u * pr.q2);
+  const uint32_t d = x - y + (kIn / 2) * pr.q2;
+  if (kIn == 12) s = csub(s, 8u * pr.q2);  // < 24q -> < 16q
+  if (kIn >= 8) {
+    s = csub(s, 4u * pr.q2);  // < 16q -> < 8q
+    s = csub(s, 2u * pr.q2);  // < 8q -> < 4q
   }
   x = csub(s, pr.q2);
   y = shoup_mul(z.x, z.y, d, pr.q);
@@ -208,6 +211,7 @@ __device__ __forceinline__ void gs_bfly(uint32_t &x, uint32_t &y, uint2 z, const
 // 32 e] in [0, 2q) (what crt_torus takes); every butterfly output is reduced to
 // [0, 2q) (one conditional subtraction on the sum, the Shoup product on the
 // difference).
+template <int kIn0>  // input bound in q (see gs_bfly)
 __device__ __forceinline__ void ntt_inv_gs(uint32_t (&x)[32], uint32_t *xbuf, const uint2 *__restrict__ gs1,
                                            const uint2 *gs2, const PrimeRT &pr, int lane) {
   constexpr int kOff[5] = {0, 16, 24, 28, 30};
@@ -220,9 +224,9 @@ __device__ __forceinline__ void ntt_inv_gs(uint32_t (&x)[32], uint32_t *xbuf, co
       if ((e & t) == 0) {
         if ((e & (2 * t - 1)) == 0) z = __ldg(gs1 + (kOff[s] + e / (2 * t)) * 32 + lane);
         if (s == 0)
-          gs_bfly<true>(x[e], x[e + t], z, pr);
+          gs_bfly<kIn0>(x[e], x[e + t], z, pr);
         else
-          gs_bfly<false>(x[e], x[e + t], z, pr);
+          gs_bfly<2>(x[e], x[e + t], z, pr);
       }
     }
   }
@@ -239,7 +243,7 @@ __device__ __forceinline__ void ntt_inv_gs(uint32_t (&x)[32], uint32_t *xbuf, co
     const int hr = 1 << s;  // half-length / 32: 1, 2, 4, 8, 16
 #pragma unroll
     for (int e = 0; e < 32; ++e) {
-      if ((e & hr) == 0) gs_bfly<false>(x[e], x[e + hr], gs2[16 / hr + e / (2 * hr)], pr);
+      if ((e & hr) == 0) gs_bfly<2>(x[e], x[e + hr], gs2[16 / hr + e / (2 * hr)], pr);
     }
   }
 }

@@ -354,6 +354,7 @@ __device__ __forceinline__ void br_consumer(const BrShared &S, const BrArgs &arg
   constexpr int kStages = br_stages<H, GT, L>();
   constexpr bool kWide = wide_mac<H, GT, L>();
   constexpr bool kTmem = tmem_mac<H, GT, L>();  // taddr: this warp's 128 TMEM columns
+  constexpr int kInvIn = kWide || kTmem ? 8 : 12;  // the inverse's input bound in q (gs_bfly)
   const int n = args.n;
   const int bar_id = 1 + g;
   const int role = h * 2 + P;
@@ -529,7 +530,7 @@ __device__ __forceinline__ void br_consumer(const BrShared &S, const BrArgs &arg
         // both outputs: one inverse code path, the accumulators swapped between uses
 #pragma unroll 1
         for (int c = 0; c < 2; ++c) {
-          ntt_inv_gs(acc0, myscr, gsi1, args.tc.gsi2[P], pr, lane);
+          ntt_inv_gs<kInvIn>(acc0, myscr, gsi1, args.tc.gsi2[P], pr, lane);
 #pragma unroll
           for (int e = 0; e < 32; ++e) {
             const uint32_t t = acc0[e];
@@ -574,7 +575,7 @@ __device__ __forceinline__ void br_consumer(const BrShared &S, const BrArgs &arg
 #pragma unroll
             for (int e = 0; e < 32; ++e) acc0[e] += src[e * 32 + lane];
           }
-          ntt_inv_gs(acc0, half, gsi1, args.tc.gsi2[P], pr, lane);
+          ntt_inv_gs<kInvIn>(acc0, half, gsi1, args.tc.gsi2[P], pr, lane);
           __syncwarp();
 #pragma unroll
           for (int e = 0; e < 16; ++e) half[e * 32 + lane] = P ? acc0[e] : acc0[16 + e];

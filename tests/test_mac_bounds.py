@@ -86,11 +86,48 @@ def test_exact_sum_matches_per_product_montgomery(rows):
 @pytest.mark.parametrize("rows,warps", [(6, 1), (6, 2), (6, 3), (4, 1), (4, 2), (4, 4)])
 def test_partial_sums_of_split_rows_stay_below_the_inverse_bound(rows, warps):
     """H warps take rows / H rows each, reduce their exact sums, and an owner warp
-    adds the H results: the worst case stays below 12q (the inverse's input bound)."""
+    adds the H results: the worst case stays below 7.2q, inside the 8q input bound
+    the inverse's first stage assumes for these shapes (the throughput shapes with
+    H = 1, 2, 3 for l = 3 and H = 1, 2, 4 for l = 2)."""
     for q in primes():
         per = rows // warps
         worst_partial = mont_redc(per * (22 * q - 1) * (q - 1), q)
         bound = per * 22 * q * q / M32 + q
         assert worst_partial < bound
-        assert warps * bound < 12 * q
+        assert warps * bound < 7.2 * q < 8 * q
         assert 6 * 22 * q * q < 5.2 * q * M32 - q * M32  # six rows reduce below 5.2q (the comment in the kernel)
+
+
+def test_per_product_montgomery_sums_stay_below_12q():
+    """The one-row-per-warp shape (H = 6) reduces every product and adds six of
+    them in its owner warp: below 12q, the first stage's other input bound."""
+    for q in primes():
+        worst = sum(mont_mul(22 * q - 1, b, q) for b in (q - 1, q - 2, 1, 12345, q // 2, q - 3))
+        assert worst < 6 * 2 * q == 12 * q
+        assert max(mont_mul(x, q - 1, q) for x in (22 * q - 1, 0, 1, q, 2 * q + 7)) < 2 * q
+
+
+@pytest.mark.parametrize("bound", [2, 8, 12])
+def test_first_inverse_stage_reduces_to_2q(bound):
+    """The inverse's Gentleman-Sande butterfly as the kernel states it: inputs below
+    bound * q; the sum reduced by conditional subtractions of 16q (bound 12 only),
+    8q and 4q (bounds 8 and 12) and a last one of 2q lands in [0, 2q); the
+    difference x - y + bound q stays in (0, 2^32)."""
+    rng = np.random.default_rng(bound)
+    for q in primes():
+        def csub(v, m):
+            return min(v, (v - m) % M32)
+        xs = [0, 1, bound * q - 1] + [int(v) for v in rng.integers(0, bound * q, 3000)]
+        ys = [bound * q - 1, 0, bound * q - 1] + [int(v) for v in rng.integers(0, bound * q, 3000)]
+        for x, y in zip(xs, ys):
+            s = (x + y) % M32
+            assert s == x + y  # no wrap
+            if bound == 12:
+                s = csub(s, 16 * q)
+            if bound >= 8:
+                s = csub(s, 8 * q)
+                s = csub(s, 4 * q)
+            s = csub(s, 2 * q)
+            assert s < 2 * q and s % q == (x + y) % q
+            d = x - y + bound * q
+            assert 0 < d < M32 and d % q == (x - y) % q
