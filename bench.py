@@ -73,8 +73,8 @@ TRAFFIC_PER_LAUNCH = {
     "br_cluster16_kernel": 62.06e6 + 2.46e6,  # 7 gates
     "br_cluster16_kernel<L=2>": 33.66e6 + 0.0e6,  # 7 gates, n = 512, l = 2
     "br_cluster8_kernel": 62.06e6 + 2.08e6,   # 8 gates
-    "br_kernel<1,6>": 66.80e6 + 3.08e6,       # 912 gates
-    "br_kernel<1,6,L=2>": 37.65e6 + 0.07e6,   # 912 gates, n = 512, l = 2
+    "br_kernel<1,6>": 66.82e6 + 3.14e6,       # 912 gates
+    "br_kernel<1,6,L=2>": 37.97e6 + 0.06e6,   # 912 gates, n = 512, l = 2
     "br_cluster8_kernel<L=2>": 33.68e6 + 6.40e6,  # 8 gates, n = 512, l = 2
     "br_kernel<4,1,L=2>": 34.26e6 + 0.001e6,      # 128 gates, n = 512, l = 2
 }
