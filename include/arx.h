@@ -38,6 +38,13 @@
  * (_ex with a non-NULL stream) calls on the same stream share that stream's
  * workspace in stream order; calls on different streams use different
  * workspaces.
+ *
+ * On-chip resources: the wide-wave blind-rotation kernels take all of an SM's
+ * shared memory and, in their twelve-warp shapes, all 512 columns of its tensor
+ * memory (tcgen05.alloc) for as long as their block runs, and free both before
+ * the block exits.  A kernel of another library that allocates tensor memory on
+ * the same SM at the same time (another stream) waits until the block is done;
+ * nothing here waits on such a kernel, so the two cannot deadlock.
  */
 #ifndef ARX_H
 #define ARX_H
